@@ -1,0 +1,305 @@
+"""Plain TT-cross with maxvol pivoting, and the TT contraction with the weights.
+
+Test infrastructure only (see the package docstring).
+
+What the paper fixes (Section IV.A-B) and what is read into it
+  * The integrand tensor is approximated by a tensor train (matrix product
+    state) built from actual tensor entries by TT-cross: sweep back and forth
+    over the cores; at each core solve a matrix cross problem M ~ M(:,J)
+    M(I,J)^{-1} M(I,:) with the other index sets fixed, choosing the rows I of
+    (quasi-)maximal volume by maxvol, starting from random column sets J.
+  * The paper leaves the details to its references.  The readings used here,
+    and implemented independently by the CUDA library:
+      - core k's fiber matrix A has rows (outer multi-index o, grid index i),
+        row number o*N + i, and the opposite index set as columns;
+      - initial rows: Gaussian elimination with partial pivoting (GEPP) run as a
+        flat tournament over blocks of ``block_rows`` rows: the current winners
+        are stacked on top of the next block and GEPP keeps the pivot rows.  A
+        column whose best pivot is at most ``theta`` times that column's largest
+        entry is skipped (numerically dependent); the kept columns set the rank;
+      - maxvol: B = A_c A_c[W]^{-1} on the kept columns, blocks visited
+        cyclically; inside a block, while max |B_ij| > 1 + tau swap row i into
+        slot j (rank-one update of B, at most rank-many swaps per block); stop
+        after every block has been visited once with no swap (then
+        |B| <= 1 + tau on the whole matrix) or after 4 * n_blocks visits;
+      - the interpolation core is G = A_c A_c[W]^{-1}; its sum over the grid
+        index is what the contraction with the quadrature weights needs;
+      - half-sweeps alternate left-to-right / right-to-left; each ends with a
+        price estimate and the sweep stops when two consecutive estimates agree
+        to ``sweep_tol`` (relative), or after ``max_half_sweeps``;
+      - ranks r_k = min(r_max, N^k, N^(d-k)); initial right sets draw distinct
+        multi-indices with SplitMix64 (slot 0 is the grid centre), or list all
+        N^(d-k) of them in lexicographic order when r_k = N^(d-k).
+  * Contraction (Section IV.A, MPS inner product): the weights are eta per axis
+    (folded into the tensor's scale), so the weighted sum of the train is the
+    product of the per-core sums W_k = sum_i G_k[:, i, :].
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .splitmix import pivot_key, splitmix64
+
+
+@dataclass
+class CrossOptions:
+    block_rows: int = 128
+    theta: float = 1e-8           # relative pivot threshold for skipping a column
+    tau: float = 0.05             # maxvol tolerance: stop when |B| <= 1 + tau
+    max_half_sweeps: int = 8
+    sweep_tol: float = 1e-7
+
+
+@dataclass
+class CrossDiag:
+    half_sweeps: int = 0
+    converged: bool = False
+    evaluations: int = 0
+    max_rank: int = 0
+    swaps: int = 0
+    maxvol_unconverged: int = 0
+    history: list = field(default_factory=list)
+    ranks: list = field(default_factory=list)
+
+
+# ----------------------------------------------------------------------------
+# ranks and initial pivots
+# ----------------------------------------------------------------------------
+
+def bond_ranks(d, n, r_max):
+    """r_0 = r_d = 1, r_k = min(r_max, N^k, N^(d-k))."""
+    return [1] + [min(r_max, n ** k, n ** (d - k)) for k in range(1, d)] + [1]
+
+
+def initial_right_set(d, n, k, size, seed, term):
+    """Distinct right multi-indices over axes k..d-1 (0-based), ``size`` of them."""
+    width = d - k
+    if n ** width == size:
+        out = []
+        for flat in range(size):
+            idx = []
+            rem = flat
+            for _ in range(width):
+                idx.append(rem % n)
+                rem //= n
+            out.append(tuple(reversed(idx)))
+        return out
+    out = [tuple([n // 2] * width)]
+    seen = {out[0]}
+    for b in range(1, size):
+        for t in range(65536):
+            cand = tuple(splitmix64(pivot_key(seed, term, k, t, b, j)) % n for j in range(k, d))
+            if cand not in seen:
+                break
+        else:
+            raise RuntimeError("initial pivot draw did not find a fresh multi-index")
+        seen.add(cand)
+        out.append(cand)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# row selection: GEPP tournament and maxvol
+# ----------------------------------------------------------------------------
+
+def gepp_select(c_mat, theta):
+    """GEPP with partial pivoting on the candidate matrix; returns (rows, cols).
+
+    Columns are taken in order.  The pivot of column c is the available row with
+    the largest |entry| of the current Schur complement (first one on ties).  If
+    |pivot| <= theta * max_i |original entry of column c|, the column is skipped.
+    """
+    s = np.array(c_mat, dtype=np.complex128, copy=True)
+    q, n = s.shape
+    if q == 0:
+        return [], []
+    colmax = (s.real ** 2 + s.imag ** 2).max(axis=0)
+    avail = np.ones(q, dtype=bool)
+    rows, cols = [], []
+    for c in range(n):
+        if not avail.any():
+            break
+        mag = s[:, c].real ** 2 + s[:, c].imag ** 2
+        mag = np.where(avail, mag, -1.0)
+        p = int(np.argmax(mag))
+        if not (mag[p] > theta * theta * colmax[c]) or mag[p] == 0.0:
+            continue
+        rows.append(p)
+        cols.append(c)
+        avail[p] = False
+        if c + 1 < n:
+            mult = s[:, c] / s[p, c]
+            mult[~avail] = 0.0
+            s[:, c + 1:] -= np.outer(mult, s[p, c + 1:])
+    return rows, cols
+
+
+def tournament_select(a_mat, block_rows, theta):
+    """Flat GEPP tournament over row blocks; returns (winner rows, kept columns)."""
+    m = a_mat.shape[0]
+    winners, cols = [], []
+    for start in range(0, m, block_rows):
+        cand = winners + list(range(start, min(m, start + block_rows)))
+        r, c = gepp_select(a_mat[cand, :], theta)
+        winners = [cand[p] for p in r]
+        cols = c
+    return winners, cols
+
+
+def maxvol_refine(a_cols, rows, block_rows, tau):
+    """Cyclic block maxvol on the kept columns, starting from ``rows``.
+
+    Returns (rows, swaps, converged).
+    """
+    m, rho = a_cols.shape
+    rows = list(rows)
+    nb = -(-m // block_rows)
+    thr = (1.0 + tau) ** 2
+    quiet = visits = swaps = 0
+    beta = 0
+    while quiet < nb and visits < 4 * nb:
+        blk = list(range(beta * block_rows, min(m, (beta + 1) * block_rows)))
+        inv = np.linalg.inv(a_cols[rows, :])
+        b_mat = a_cols[blk, :] @ inv
+        swapped = False
+        for _ in range(rho):
+            mag = b_mat.real ** 2 + b_mat.imag ** 2
+            flat = int(np.argmax(mag))
+            i, j = divmod(flat, rho)
+            if not (mag[i, j] > thr):
+                break
+            rows[j] = blk[i]
+            piv = b_mat[i, j]
+            col = b_mat[:, j].copy()
+            row = b_mat[i, :].copy()
+            row[j] -= 1.0
+            b_mat -= np.outer(col, row) / piv
+            swapped = True
+            swaps += 1
+        quiet = 0 if swapped else quiet + 1
+        visits += 1
+        beta = (beta + 1) % nb
+    return rows, swaps, quiet >= nb
+
+
+# ----------------------------------------------------------------------------
+# one core of a half-sweep
+# ----------------------------------------------------------------------------
+
+def _fiber(tensor, d, n, k, outer, cols, direction):
+    """Fiber matrix of core k: rows (o, i) -> o*N + i, columns = ``cols``.
+
+    direction 'lr': full index = outer[o] + (i,) + cols[c]
+    direction 'rl': full index = cols[c] + (i,) + outer[o]
+    """
+    no, nc = len(outer), len(cols)
+    idx = np.empty((no, n, nc, d), dtype=np.int64)
+    outer_a = np.array(outer, dtype=np.int64).reshape(no, -1)
+    cols_a = np.array(cols, dtype=np.int64).reshape(nc, -1)
+    grid_i = np.arange(n, dtype=np.int64)
+    if direction == "lr":
+        idx[..., :k] = outer_a[:, None, None, :]
+        idx[..., k] = grid_i[None, :, None]
+        idx[..., k + 1:] = cols_a[None, None, :, :]
+    else:
+        idx[..., :k] = cols_a[None, None, :, :]
+        idx[..., k] = grid_i[None, :, None]
+        idx[..., k + 1:] = outer_a[:, None, None, :]
+    return tensor(idx).reshape(no * n, nc)
+
+
+def core_select(tensor, d, n, k, outer, cols, direction, opts, diag):
+    """Select rows of core k's fiber; returns (new index set, summed interpolant)."""
+    a_mat = _fiber(tensor, d, n, k, outer, cols, direction)
+    diag.evaluations += a_mat.size
+    rows, keep = tournament_select(a_mat, opts.block_rows, opts.theta)
+    if not rows:
+        raise FloatingPointError("fiber matrix has numerical rank 0")
+    a_cols = a_mat[:, keep]
+    rows, swaps, ok = maxvol_refine(a_cols, rows, opts.block_rows, opts.tau)
+    diag.swaps += swaps
+    diag.maxvol_unconverged += 0 if ok else 1
+    g = a_cols @ np.linalg.inv(a_cols[rows, :])
+    gsum = g.reshape(len(outer), n, len(rows)).sum(axis=1)
+    if direction == "lr":
+        new_set = [tuple(outer[w // n]) + (w % n,) for w in rows]
+    else:
+        new_set = [(w % n,) + tuple(outer[w // n]) for w in rows]
+    return new_set, gsum
+
+
+def core_sum(tensor, d, n, k, outer, direction, diag):
+    """End core of a half-sweep: sum over its grid index, one value per outer index."""
+    a_mat = _fiber(tensor, d, n, k, outer, [()], direction)
+    diag.evaluations += a_mat.size
+    return a_mat.reshape(len(outer), n).sum(axis=1)
+
+
+# ----------------------------------------------------------------------------
+# the sweeps
+# ----------------------------------------------------------------------------
+
+def tt_cross_sum(tensor, r_max, seed, term=0, opts=None):
+    """TT-cross approximation of sum over the grid of ``tensor``; returns (sum, diag)."""
+    opts = opts or CrossOptions()
+    d, n = tensor.d, tensor.n
+    ranks = bond_ranks(d, n, r_max)
+    lsets = [None] * (d + 1)
+    rsets = [None] * (d + 1)
+    lsets[0] = [()]
+    rsets[d] = [()]
+    for k in range(1, d):
+        rsets[k] = initial_right_set(d, n, k, ranks[k], seed, term)
+    diag = CrossDiag()
+    prev = None
+    est = 0j
+    for s in range(opts.max_half_sweeps):
+        if s % 2 == 0:
+            v = np.ones(1, dtype=np.complex128)
+            for k in range(d - 1):
+                lsets[k + 1], gsum = core_select(tensor, d, n, k, lsets[k], rsets[k + 1], "lr", opts, diag)
+                v = v @ gsum
+            est = complex(v @ core_sum(tensor, d, n, d - 1, lsets[d - 1], "lr", diag))
+        else:
+            v = np.ones(1, dtype=np.complex128)
+            for k in range(d - 1, 0, -1):
+                rsets[k], gsum = core_select(tensor, d, n, k, rsets[k + 1], lsets[k], "rl", opts, diag)
+                v = gsum.T @ v
+            est = complex(core_sum(tensor, d, n, 0, rsets[1], "rl", diag) @ v)
+        diag.half_sweeps = s + 1
+        diag.history.append(est)
+        sets = lsets[1:d] if s % 2 == 0 else rsets[1:d]
+        diag.ranks = [len(x) for x in sets]
+        diag.max_rank = max([diag.max_rank, 1] + diag.ranks)
+        if d == 1:
+            diag.converged = True
+            break
+        if prev is not None and abs(est - prev) <= opts.sweep_tol * abs(est):
+            diag.converged = True
+            break
+        prev = est
+    return est, diag
+
+
+def tt_price(problem, opts=None):
+    """Price = Re(sum over terms of scale * TT-cross sum); returns (price, imag, diags)."""
+    from .integrand import tensors_for
+
+    acc = 0j
+    diags = []
+    for term, t in enumerate(tensors_for(problem)):
+        est, dg = tt_cross_sum(t, int(problem.max_rank), int(problem.seed), term, opts)
+        acc += t.scale * est
+        diags.append(dg)
+    return acc.real, acc.imag, diags
+
+
+def dense_from_cores(cores):
+    """Brute-force TT -> dense tensor (for pinning the contraction on tiny cases)."""
+    out = cores[0]
+    for c in cores[1:]:
+        out = np.tensordot(out, c, axes=([-1], [0]))
+    return out.reshape(out.shape[1:-1])
