@@ -1,0 +1,302 @@
+"""Benchmark: option prices per second for the d=5 call on the minimum (N=128, rank 32).
+
+Workload: a batch of B seeded problems of the five-asset min-call family
+(S0_j~U[90,110], sigma_j~U[0.15,0.35], equicorrelation 0.3, K=100, r=0.02, T=1,
+alpha=-1.5, N=128 on [-40,40], TT rank 32), priced in one launch per step on the
+mixed path (FP32 integrand/elimination/maxvol, FP64 phase, solve and sums).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl reference]
+
+Prints one JSON line.  `value` times only the device work (tt_price_run, the
+problems already resident in HBM) with CUDA events on the launching stream, L2
+flushed between steps; `e2e` times tt_price_evaluate with host buffers (host
+preparation, one host-to-device copy, kernels, one device-to-host copy).
+The CPU baseline is the FP64 oracle (plain TT-cross in NumPy) on a bounded
+sample of the same problems, on the host cores, in spawned worker processes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "option prices/sec at <=1e-4 rel. error vs FP64 oracle"
+UNIT = "prices/s"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5, derived
+
+
+def workload_problems(batch, rank_offset=0):
+    from paper_2203_02804_gb300 import inputs
+
+    return inputs.five_asset_batch(batch, index=1 + 10 * rank_offset)
+
+
+def workload_config(batch, precision="mixed"):
+    return {"workload": "d5-min-call", "d": 5, "n_grid": 128, "trunc_L": 40.0, "max_rank": 32,
+            "batch_per_gpu": batch, "precision": precision,
+            "l2": "flushed (256 MiB write) between timed steps"}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) legs
+# ----------------------------------------------------------------------------
+
+def _oracle_one(args):
+    import numpy as np  # noqa: F401  (thread env set by the parent before spawn)
+
+    from oracle import ttcross
+
+    p = args
+    price, _, _ = ttcross.tt_price(p)
+    return price
+
+
+def oracle_prices(problems, workers):
+    import multiprocessing as mp
+
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("MKL_NUM_THREADS", "1")
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        out = pool.map(_oracle_one, problems, chunksize=1)
+    return out, time.perf_counter() - t0
+
+
+def cpu_workers():
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same metric and config."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    workers = cpu_workers()
+    per_step = workers
+    probs = workload_problems(per_step * (args.warmup + args.steps))
+    times = []
+    for s in range(args.warmup + args.steps):
+        chunk = probs[s * per_step:(s + 1) * per_step]
+        _, dt = oracle_prices(chunk, workers)
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(per_step, "fp64-oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"{per_step} problems per step, one per worker process"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+
+    # CPU baseline first (spawned workers, before this process does much CUDA work)
+    sample = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workers = cpu_workers()
+        sample_probs = workload_problems(args.batch)[:max(workers, args.cpu_sample)]
+        sample_prices, sample_dt = oracle_prices(sample_probs, workers)
+        sample = (sample_probs, sample_prices, sample_dt, workers)
+
+    from paper_2203_02804_gb300 import build, ttprice
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    problems = workload_problems(args.batch, rank_offset=rank)
+    pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=args.batch,
+                        precision=args.precision, device=local, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # ---- device-resident timing: tt_price_run only ----
+    rc = pr.prepare(problems)
+    assert rc == ttprice.TT_OK, ttprice.status_string(rc)
+    for _ in range(args.warmup):
+        assert pr.run() == ttprice.TT_OK
+    torch.cuda.synchronize()
+    rc, prices, diags = pr.results()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)
+            ev[s][0].record(stream)
+            assert pr.run() == ttprice.TT_OK
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    rc, prices, diags = pr.results()
+    flops_per_step = sum(d.flops for d in diags)
+    evals_per_step = sum(d.evaluations for d in diags)
+    value = args.batch * world * args.steps / total_s
+
+    # ---- end to end through the public API: tt_price_evaluate with host buffers ----
+    for _ in range(max(1, args.warmup // 2)):
+        pr.evaluate(problems)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc_e, p_e, _ = pr.evaluate(problems)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d, d2h = pr.transfer_bytes()
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = args.batch * world * args.steps / e2e_s
+    pr.close()
+
+    if rank == 0:
+        clocks = clk.summary()
+        kernel_s = total_s / args.steps
+        achieved = flops_per_step / kernel_s / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": workload_config(args.batch, args.precision),
+            "roofline": {"bound": "alu", "achieved": achieved,
+                         "peak": FP32_PEAK_TFLOPS if args.precision == "mixed" else 1.26,
+                         "unit": "TFLOP/s",
+                         "frac": achieved / (FP32_PEAK_TFLOPS if args.precision == "mixed" else 1.26),
+                         "traffic": None,
+                         "kernel": f"tt_cross_kernel<{'float' if args.precision == 'mixed' else 'double'}>",
+                         "flops_per_launch": flops_per_step,
+                         "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "evaluations_per_price": evals_per_step / args.batch,
+            "status_counts": {str(s): sum(1 for d in diags if d.status == s)
+                              for s in sorted({d.status for d in diags})},
+        }
+        if sample is not None:
+            sp, sprices, sdt, workers = sample
+            n = len(sp)
+            rel = [abs(prices[i] / sprices[i] - 1.0) for i in range(n)]
+            line["cpu_baseline"] = {"value": n / sdt, "unit": UNIT, "cores": workers, "kind": "oracle",
+                                    "sample": f"first {n} problems of the batch, FP64 NumPy TT-cross, "
+                                              f"one process per core"}
+            line["parity"] = {"vs": "FP64 oracle TT-cross, same problems", "n": n,
+                              "max_rel_err": max(rel), "tol": 1e-4 if args.precision == "mixed" else 1e-6}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-sample", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

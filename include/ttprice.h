@@ -1,0 +1,150 @@
+/*
+ * ttprice -- tensor-train Fourier pricer for multi-asset European options
+ * (arXiv 2203.02804), GB300 / sm_103a.
+ *
+ * What it computes.  For d correlated GBM assets (Section II.A: dS^j = r S^j dt
+ * + sigma_j S^j dW^j with annualised covariance Cov) the price of a call on the
+ * minimum (Eq. minpayoff) is the damped d-dimensional Fourier integral of
+ * Eq. (main): V = e^{-rT} (2 pi)^{-d} int phi_T(-z) vhat(z) du on
+ * Im z = delta, discretised on an N^d midpoint grid per axis as in Eq. (discr).
+ * The N^d tensor of integrand values is put into tensor-train (matrix product
+ * state) form by TT-cross with maxvol pivoting (Section IV.B) and contracted with
+ * the quadrature weights (Section IV.A), at O(d N r^2) integrand evaluations.
+ * The call on the maximum (not in the paper) is the sum of d such trains, one per
+ * asset that can be the maximum.
+ *
+ * Conventions.
+ *  - All arrays passed in are host memory owned by the caller and read only
+ *    during the call.  Prices and diagnostics are written to caller-owned host
+ *    memory.  The library owns all device memory it allocates; a caller may
+ *    instead hand it a device workspace (tt_options.workspace).
+ *  - Functions return a tt_status; tt_price_evaluate returns the worst status
+ *    over the batch and never aborts the batch for one bad problem: a problem
+ *    that fails validation or collapses numerically gets price NaN and its own
+ *    status in tt_diag.
+ *  - A handle is not thread-safe; all work runs on tt_options.cuda_stream.
+ */
+#ifndef TTPRICE_H
+#define TTPRICE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tt_pricer tt_pricer; /* opaque, library-owned */
+
+typedef enum {
+  TT_OK = 0,
+  TT_WARN_NOT_CONVERGED = 1, /* sweep cap reached before the stop rule held */
+  TT_ERR_INVALID = -1,       /* bad argument or size */
+  TT_ERR_NOT_PD = -2,        /* covariance failed an FP64 Cholesky (paper assumes PD, Sec. II.A) */
+  TT_ERR_STRIP = -3,         /* damping outside the payoff transform's strip (Sec. III.C) */
+  TT_ERR_CAPACITY = -4,      /* exceeds the sizes the handle was created for */
+  TT_ERR_CUDA = -5,          /* a CUDA call failed */
+  TT_ERR_NUMERIC = -6        /* fiber matrix of numerical rank 0, or a non-finite price */
+} tt_status;
+
+typedef enum { TT_MIN_CALL = 0, TT_MAX_CALL = 1 } tt_payoff;
+
+/* TT_FP64: every step in FP64.
+ * TT_MIXED: integrand values, elimination and maxvol in FP32 complex; the phase
+ * and exponent arguments, the interpolation solve and the contraction in FP64. */
+typedef enum { TT_FP64 = 0, TT_MIXED = 1 } tt_precision;
+
+typedef struct {
+  int max_d;            /* largest number of assets                        (1..255)  */
+  int max_n;            /* largest grid size N per axis                    (2..4096) */
+  int max_rank;         /* largest TT rank                                 (1..64)   */
+  int max_batch;        /* largest number of problems per evaluate call            */
+  tt_precision precision;
+  int max_half_sweeps;  /* 0 -> 8 (alternating left-to-right / right-to-left)       */
+  double sweep_tol;     /* <= 0 -> 1e-7 (FP64) or 1e-5 (mixed): relative change of
+                           the price estimate between half-sweeps that stops a job */
+  double rank_tol;      /* <= 0 -> 1e-8 (FP64) or 1e-5 (mixed): a column whose
+                           elimination pivot is below rank_tol times the column's
+                           largest entry is dropped (numerically dependent)        */
+  double maxvol_tol;    /* <= 0 -> 0.05: maxvol stops when all |B_ij| <= 1 + tol  */
+  int block_rows;       /* 0 -> 128: rows per elimination/maxvol block;
+                           needs max_rank <= block_rows <= 256 - max_rank          */
+  int device;           /* CUDA device ordinal                                     */
+  void* cuda_stream;    /* cudaStream_t to run on; NULL = legacy default stream    */
+  void* workspace;      /* optional device buffer of tt_workspace_bytes() bytes,
+                           owned by the caller; NULL = the library allocates       */
+  size_t workspace_bytes;
+} tt_options;
+
+typedef struct {
+  int d;                 /* number of assets                                       */
+  const double* spot;    /* [d] S0_j > 0                                           */
+  const double* cov;     /* [d*d] row-major annualised covariance, SPD             */
+  double rate;           /* r                                                      */
+  double maturity;       /* T > 0                                                  */
+  double strike;         /* K > 0                                                  */
+  int payoff;            /* tt_payoff                                              */
+  const double* damping; /* [d] alpha_j.  Min-call: Im z_j = -alpha_j, needs
+                            -alpha_j > 0 and sum_j -alpha_j > 1.  Max-call term j:
+                            Im z_j = 1 + |alpha_j| and Im z_l = -|alpha_l| (l != j),
+                            needs every alpha_l != 0                               */
+  int n_grid;            /* N grid points per axis (midpoints of [-L, L])          */
+  double trunc_L;        /* L > 0                                                  */
+  int max_rank;          /* TT rank cap for this problem (<= tt_options.max_rank)  */
+  unsigned long long seed; /* initial random pivots (SplitMix64), per problem       */
+} tt_problem;
+
+typedef struct {
+  int status;            /* tt_status of this problem                              */
+  int half_sweeps;       /* largest number of half-sweeps over its trains          */
+  int final_rank_max;    /* largest TT rank after rank reduction                   */
+  int terms;             /* trains summed: 1 (min-call) or d (max-call)            */
+  long long evaluations; /* integrand evaluations, fiber entries counted once      */
+  double imag_part;      /* Im of the discrete sum; 0 up to the TT error           */
+  double flops;          /* arithmetic of the elimination, maxvol, interpolation
+                            and integrand steps, by formula (see DESIGN notes)     */
+} tt_diag;
+
+/* Create a pricer for problems up to the given sizes on opt->device.  Allocates
+ * all device memory the handle needs (unless opt->workspace is given).
+ * Returns TT_OK, TT_ERR_INVALID or TT_ERR_CUDA; *out is NULL on failure. */
+int tt_price_create(const tt_options* opt, tt_pricer** out);
+
+/* Device bytes tt_price_create needs for these options (for a caller-owned
+ * workspace).  0 if the options are invalid. */
+size_t tt_workspace_bytes(const tt_options* opt);
+
+/* Price count (<= max_batch) problems.  Blocking: returns after prices[] and
+ * diag[] (nullable) are written.  Equivalent to tt_price_prepare +
+ * tt_price_run + tt_price_results. */
+int tt_price_evaluate(tt_pricer* h, const tt_problem* probs, int count, double* prices,
+                      tt_diag* diag);
+
+/* Validate and derive the per-train parameters on the host (FP64), and copy them
+ * to the device (one asynchronous host-to-device copy on the handle's stream).
+ * Per-problem validation failures are recorded, not returned as errors; the
+ * return value is TT_ERR_INVALID/CAPACITY/CUDA only for batch-level failures. */
+int tt_price_prepare(tt_pricer* h, const tt_problem* probs, int count);
+
+/* Launch the pricing kernels for the prepared batch on the handle's stream and
+ * return without waiting.  Can be repeated (the batch stays resident). */
+int tt_price_run(tt_pricer* h);
+
+/* Copy the results of the last run to the host, wait for them, and write
+ * prices[count] and diag[count] (nullable).  Returns the worst status. */
+int tt_price_results(tt_pricer* h, double* prices, tt_diag* diag);
+
+/* Bytes the last tt_price_prepare copied host-to-device and the last
+ * tt_price_results copied device-to-host (for end-to-end accounting). */
+int tt_price_transfer_bytes(const tt_pricer* h, size_t* h2d, size_t* d2h);
+
+/* Release everything the handle owns.  NULL-safe. */
+void tt_price_destroy(tt_pricer* h);
+
+/* Static text for a status code. */
+const char* tt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTPRICE_H */

@@ -1,0 +1,787 @@
+// Tensor-train Fourier pricer (arXiv 2203.02804) for GB300 / sm_103a:
+// the C ABI declared in include/ttprice.h, the host-side preparation and the
+// persistent TT-cross kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ttprice.h"
+#include "ttprice_device.cuh"
+
+namespace ttp {
+
+// ---------------------------------------------------------------------------
+// the persistent kernel: one CTA = one TT-cross job at a time
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __restrict__ jobs,
+                                                            const double* __restrict__ params,
+                                                            const int* __restrict__ order, int njobs,
+                                                            int* counter, JobResult* results,
+                                                            char* scratch, Layout lay, SmemLayout sl,
+                                                            Knobs kn) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double dscr[32];
+  const int tid = threadIdx.x;
+  Ctx<R> x;
+  char* base = scratch + (size_t)blockIdx.x * lay.stride;
+  x.dmax = lay.dmax;
+  x.nmax = lay.nmax;
+  x.rall = lay.rmax;
+  x.u = reinterpret_cast<double*>(base + lay.u);
+  x.lam = reinterpret_cast<double*>(base + lay.lam);
+  x.om = reinterpret_cast<double2*>(base + lay.om);
+  x.lset = reinterpret_cast<uint16_t*>(base + lay.lset);
+  x.rset = reinterpret_cast<uint16_t*>(base + lay.rset);
+  x.lstate = reinterpret_cast<double*>(base + lay.lstate);
+  x.rstate = reinterpret_cast<double*>(base + lay.rstate);
+  x.lvec = reinterpret_cast<double*>(base + lay.lvec);
+  x.rvec = reinterpret_cast<double*>(base + lay.rvec);
+  {
+    R* pr = reinterpret_cast<R*>(base + lay.pair);
+    const size_t plane = (size_t)lay.rmax * lay.rmax;
+    x.pE0 = pr;
+    x.pH = pr + plane;
+    x.pS0 = pr + 2 * plane;
+    x.pOre = pr + 3 * plane;
+    x.pOim = pr + 4 * plane;
+  }
+  x.P = reinterpret_cast<cpx<R>*>(base + lay.P);
+  x.sacc = reinterpret_cast<double2*>(base + lay.sacc);
+  x.vchain = reinterpret_cast<double2*>(base + lay.chain);
+  x.ychain = x.vchain + lay.rmax;
+  x.sw = reinterpret_cast<cpx<R>*>(smem + sl.sw);
+  x.M = reinterpret_cast<cpx<R>*>(smem + sl.m);
+  {
+    R* tb = reinterpret_cast<R*>(smem + sl.tab);
+    x.tl = tb;
+    x.tu = tb + lay.nmax;
+    x.tor = tb + 2 * lay.nmax;
+    x.toi = tb + 3 * lay.nmax;
+  }
+  x.colmax = reinterpret_cast<R*>(smem + sl.colmax);
+  x.wrow = reinterpret_cast<int*>(smem + sl.wrow);
+  x.wnew = reinterpret_cast<int*>(smem + sl.wnew);
+  x.jp = reinterpret_cast<int*>(smem + sl.jp);
+  x.selr = reinterpret_cast<int*>(smem + sl.selr);
+  x.selc = reinterpret_cast<int*>(smem + sl.selc);
+  x.used = smem + sl.used;
+  x.redv = reinterpret_cast<R*>(smem + sl.redv);
+  x.redi = reinterpret_cast<int*>(smem + sl.redi);
+  x.swcol = reinterpret_cast<cpx<R>*>(smem + sl.swcol);
+  x.swrow = reinterpret_cast<cpx<R>*>(smem + sl.swrow);
+  x.lsz = reinterpret_cast<int*>(smem + sl.lsz);
+  x.rsz = reinterpret_cast<int*>(smem + sl.rsz);
+  x.misc = reinterpret_cast<int*>(smem + sl.misc);
+
+  for (int guard = 0; guard < njobs + 1; ++guard) {  // at most njobs jobs per CTA
+    if (tid == 0) x.misc[MISC_JOB] = atomicAdd(counter, 1);
+    __syncthreads();
+    const int slot = x.misc[MISC_JOB];
+    if (slot >= njobs) break;
+    const int jid = order[slot];
+    const JobDesc jd = jobs[jid];
+    const double* prm = params + jd.param_off;
+    x.d = jd.d;
+    x.n = jd.n;
+    x.rmax = jd.rmax;
+    x.cauchy = jd.cauchy;
+    x.D0 = (R)jd.D0;
+    x.T = jd.T;
+    x.cov = prm;
+    x.flops = 0.0;
+    x.evals = 0;
+    if (tid == 0) {
+      x.misc[MISC_FAIL] = 0;
+      x.misc[MISC_DRAW] = 0;
+    }
+    __syncthreads();
+    double norm_sum = 0.0;
+    job_setup(x, jd, prm, dscr, norm_sum);
+
+    double2 est = make_double2(0.0, 0.0), prev = make_double2(0.0, 0.0);
+    int status = x.misc[MISC_DRAW] ? ST_INVALID : ST_NOT_CONVERGED;
+    int hs = 0, maxrank = 1;
+    const int d = jd.d;
+    for (int s = 0; s < kn.max_half_sweeps && status == ST_NOT_CONVERGED; ++s) {
+      if (tid == 0) x.vchain[0] = make_double2(1.0, 0.0);
+      __syncthreads();
+      if ((s & 1) == 0) {
+        for (int k = 0; k + 1 < d; ++k) {
+          const int rho = core_select(x, kn, k, DIR_LR);
+          maxrank = max(maxrank, rho);
+          if (x.misc[MISC_FAIL]) break;
+        }
+        if (!x.misc[MISC_FAIL]) est = core_sum(x, d - 1, DIR_LR, dscr);
+      } else {
+        for (int k = d - 1; k >= 1; --k) {
+          const int rho = core_select(x, kn, k, DIR_RL);
+          maxrank = max(maxrank, rho);
+          if (x.misc[MISC_FAIL]) break;
+        }
+        if (!x.misc[MISC_FAIL]) est = core_sum(x, 0, DIR_RL, dscr);
+      }
+      hs = s + 1;
+      if (x.misc[MISC_FAIL] || !isfinite(est.x) || !isfinite(est.y)) {
+        status = ST_NUMERIC;
+        break;
+      }
+      if (d == 1) {
+        status = ST_OK;
+        break;
+      }
+      if (s >= 1) {
+        const double dx = est.x - prev.x, dy = est.y - prev.y;
+        if (sqrt(dx * dx + dy * dy) <= kn.sweep_tol * sqrt(est.x * est.x + est.y * est.y)) {
+          status = ST_OK;
+          break;
+        }
+      }
+      prev = est;
+    }
+    if (tid == 0) {
+      JobResult r;
+      r.est_re = est.x;
+      r.est_im = est.y;
+      r.norm_sum = norm_sum;
+      r.flops = x.flops;
+      r.evaluations = x.evals;
+      r.status = status;
+      r.half_sweeps = hs;
+      r.max_rank = maxrank;
+      r.maxvol_capped = 0;
+      results[jid] = r;
+    }
+    __syncthreads();
+  }
+}
+
+// per-instance combination of the trains: price = sum Re(weight sign e^{logscale+norms} est)
+__global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResult* __restrict__ jres,
+                                const int* __restrict__ first, const int* __restrict__ count,
+                                const int* __restrict__ hstatus, int ninst, InstanceResult* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  InstanceResult r;
+  r.price = 0.0;
+  r.imag = 0.0;
+  r.flops = 0.0;
+  r.evaluations = 0;
+  r.half_sweeps = 0;
+  r.max_rank = 0;
+  r.terms = count[i];
+  int worst_err = 0, worst_warn = 0;
+  if (hstatus[i] < 0) worst_err = hstatus[i];
+  for (int t = 0; t < count[i]; ++t) {
+    const int j = first[i] + t;
+    const JobDesc& jd = jobs[j];
+    const JobResult& q = jres[j];
+    const double sc = jd.weight * jd.sign * exp(jd.logscale + q.norm_sum);
+    r.price += sc * q.est_re;
+    r.imag += sc * q.est_im;
+    r.flops += q.flops;
+    r.evaluations += q.evaluations;
+    r.half_sweeps = max(r.half_sweeps, q.half_sweeps);
+    r.max_rank = max(r.max_rank, q.max_rank);
+    if (q.status < 0 && (worst_err == 0 || q.status < worst_err)) worst_err = q.status;
+    if (q.status > worst_warn) worst_warn = q.status;
+  }
+  r.status = worst_err != 0 ? worst_err : worst_warn;
+  if (r.status < 0 || !isfinite(r.price)) {
+    if (r.status >= 0) r.status = ST_NUMERIC;
+    r.price = nan("");
+  }
+  out[i] = r;
+}
+
+}  // namespace ttp
+
+// ===========================================================================
+// host side
+// ===========================================================================
+namespace {
+
+using ttp::InstanceResult;
+using ttp::JobDesc;
+using ttp::JobResult;
+using ttp::Knobs;
+using ttp::Layout;
+using ttp::SmemLayout;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Resolved {
+  tt_options o;
+  Knobs kn;
+  int max_jobs;
+  size_t max_params;
+};
+
+bool resolve(const tt_options* in, Resolved* r) {
+  if (!in) return false;
+  r->o = *in;
+  tt_options& o = r->o;
+  if (o.max_d < 1 || o.max_d > 255) return false;
+  if (o.max_n < 2 || o.max_n > 4096) return false;
+  if (o.max_rank < 1 || o.max_rank > 64) return false;
+  if (o.max_batch < 1 || o.max_batch > (1 << 22)) return false;
+  if (o.precision != TT_FP64 && o.precision != TT_MIXED) return false;
+  if (o.block_rows == 0) o.block_rows = 128;
+  if (o.block_rows < o.max_rank || o.block_rows + o.max_rank > ttp::kThreads) return false;
+  if (o.max_half_sweeps == 0) o.max_half_sweeps = 8;
+  if (o.max_half_sweeps < 1 || o.max_half_sweeps > 1000) return false;
+  const bool f64 = o.precision == TT_FP64;
+  if (!(o.sweep_tol > 0)) o.sweep_tol = f64 ? 1e-7 : 1e-5;
+  if (!(o.rank_tol > 0)) o.rank_tol = f64 ? 1e-8 : 1e-5;
+  if (!(o.maxvol_tol > 0)) o.maxvol_tol = 0.05;
+  if (!std::isfinite(o.sweep_tol) || !std::isfinite(o.rank_tol) || !std::isfinite(o.maxvol_tol))
+    return false;
+  r->kn.theta = o.rank_tol;
+  r->kn.tau = o.maxvol_tol;
+  r->kn.sweep_tol = o.sweep_tol;
+  r->kn.max_half_sweeps = o.max_half_sweeps;
+  r->kn.block_rows = o.block_rows;
+  const long long mj = (long long)o.max_batch * o.max_d;
+  if (mj > (1 << 24)) return false;
+  r->max_jobs = (int)mj;
+  r->max_params = (size_t)r->max_jobs * ((size_t)o.max_d * o.max_d + 3 * (size_t)o.max_d);
+  return true;
+}
+
+Layout make_layout(const tt_options& o, bool f64) {
+  Layout L;
+  const size_t A = 256;
+  const size_t d = o.max_d, n = o.max_n, r = o.max_rank;
+  const size_t rs = f64 ? 8 : 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes, A);
+    return at;
+  };
+  L.u = take(n * 8);
+  L.lam = take(d * n * 8);
+  L.om = take(d * n * 16);
+  L.lset = take((d + 1) * r * d * 2);
+  L.rset = take((d + 1) * r * d * 2);
+  L.lstate = take(r * 8 * 8);
+  L.rstate = take(r * 8 * 8);
+  L.lvec = take(r * d * 8);
+  L.rvec = take(r * d * 8);
+  L.pair = take(5 * r * r * rs);
+  L.P = take(r * r * 2 * rs);
+  L.sacc = take(r * r * 16);
+  L.chain = take(2 * r * 16);
+  L.stride = align_up(off, A);
+  L.dmax = (int)d;
+  L.nmax = (int)n;
+  L.rmax = (int)r;
+  return L;
+}
+
+SmemLayout make_smem(const tt_options& o, bool f64) {
+  SmemLayout S;
+  const int rs = f64 ? 8 : 4, cs = 2 * rs;
+  const int r = o.max_rank, b = o.block_rows, n = o.max_n, d = o.max_d;
+  int sw_elems = std::max((r + b) * r, 2 * r * r);
+  sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + cs - 1) / cs);
+  int off = 0;
+  auto take = [&](int bytes) {
+    int at = off;
+    off = (int)align_up(off + bytes, 16);
+    return at;
+  };
+  S.sw_elems = sw_elems;
+  S.sw = take(sw_elems * cs);
+  S.m = take(r * r * cs);
+  S.tab = take(4 * n * rs);
+  S.colmax = take(r * rs);
+  S.wrow = take(r * 4);
+  S.wnew = take(r * 4);
+  S.jp = take(r * 4);
+  S.selr = take(r * 4);
+  S.selc = take(r * 4);
+  S.used = take(ttp::kThreads);
+  S.redv = take(2 * ttp::kWarps * rs);
+  S.redi = take(2 * ttp::kWarps * 4);
+  S.swcol = take(std::max(b * cs, r * 16));
+  S.swrow = take(2 * r * cs);
+  S.lsz = take((d + 1) * 4);
+  S.rsz = take((d + 1) * 4);
+  S.misc = take(16 * 4);
+  S.total = off;
+  return S;
+}
+
+struct DevLayout {  // offsets inside the device workspace
+  size_t stage, stage_bytes, jres, ires, counter, scratch, total;
+  size_t o_jobs, o_params, o_order, o_first, o_count, o_hstatus;  // inside the stage block
+};
+
+DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
+  DevLayout D;
+  const size_t A = 256;
+  size_t s = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = s;
+    s = align_up(s + bytes, A);
+    return at;
+  };
+  D.o_jobs = take(sizeof(JobDesc) * R.max_jobs);
+  D.o_params = take(sizeof(double) * R.max_params);
+  D.o_order = take(sizeof(int) * R.max_jobs);
+  D.o_first = take(sizeof(int) * R.o.max_batch);
+  D.o_count = take(sizeof(int) * R.o.max_batch);
+  D.o_hstatus = take(sizeof(int) * R.o.max_batch);
+  D.stage_bytes = s;
+  size_t off = 0;
+  auto take2 = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes, A);
+    return at;
+  };
+  D.stage = take2(D.stage_bytes);
+  D.jres = take2(sizeof(JobResult) * R.max_jobs);
+  D.ires = take2(sizeof(InstanceResult) * R.o.max_batch);
+  D.counter = take2(sizeof(int) * 4);
+  D.scratch = take2(L.stride * (size_t)grid);
+  D.total = off;
+  return D;
+}
+
+int grid_for(const tt_options& o, const SmemLayout& S, int* grid_out) {
+  int dev_sms = 0;
+  if (cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess)
+    return TT_ERR_CUDA;
+  int per_sm = 0;
+  cudaError_t e;
+  if (o.precision == TT_FP64) {
+    e = cudaFuncSetAttribute(ttp::tt_cross_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             S.total);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttp::tt_cross_kernel<double>,
+                                                        ttp::kThreads, S.total);
+  } else {
+    e = cudaFuncSetAttribute(ttp::tt_cross_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             S.total);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttp::tt_cross_kernel<float>,
+                                                        ttp::kThreads, S.total);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TT_ERR_CUDA;
+  }
+  if (per_sm < 1) return TT_ERR_CAPACITY;
+  *grid_out = dev_sms * per_sm;
+  return TT_OK;
+}
+
+// ---- per-problem validation and derivation (FP64, host) ----
+bool finite_all(const double* p, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+bool cholesky_ok(const double* c, int d) {
+  std::vector<double> l((size_t)d * d, 0.0);
+  double scale = 0.0;
+  for (int i = 0; i < d * d; ++i) scale = std::max(scale, std::fabs(c[i]));
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(c[i * d + j] - c[j * d + i]) > 1e-12 * scale) return false;
+  for (int j = 0; j < d; ++j) {
+    double s = c[j * d + j];
+    for (int k = 0; k < j; ++k) s -= l[j * d + k] * l[j * d + k];
+    if (!(s > 0.0)) return false;
+    const double ljj = std::sqrt(s);
+    l[j * d + j] = ljj;
+    for (int i = j + 1; i < d; ++i) {
+      double t = c[i * d + j];
+      for (int k = 0; k < j; ++k) t -= l[i * d + k] * l[j * d + k];
+      l[i * d + j] = t / ljj;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+struct tt_pricer {
+  Resolved R;
+  Layout lay;
+  SmemLayout sml;
+  DevLayout dl;
+  int grid;
+  cudaStream_t stream;
+  bool own_ws;
+  char* ws;
+  char* h_stage;           // pinned, capacity layout, filled by validation
+  char* h_pack;            // pinned, packed copy that is sent to the device
+  InstanceResult* h_ires;  // pinned
+  int count, njobs;
+  size_t p_jobs, p_params, p_order, p_first, p_count, p_hstatus, p_bytes;  // packed offsets
+  size_t last_h2d, last_d2h;
+};
+
+namespace {
+
+int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
+  const tt_options& o = h->R.o;
+  if (count < 0 || count > o.max_batch || (count > 0 && !probs)) return TT_ERR_INVALID;
+  char* st = h->h_stage;
+  JobDesc* jobs = reinterpret_cast<JobDesc*>(st + h->dl.o_jobs);
+  double* params = reinterpret_cast<double*>(st + h->dl.o_params);
+  int* order = reinterpret_cast<int*>(st + h->dl.o_order);
+  int* first = reinterpret_cast<int*>(st + h->dl.o_first);
+  int* cnt = reinterpret_cast<int*>(st + h->dl.o_count);
+  int* hstat = reinterpret_cast<int*>(st + h->dl.o_hstatus);
+  int nj = 0;
+  size_t poff = 0;
+  std::vector<double> cost;
+  cost.reserve((size_t)count * 2);
+  for (int i = 0; i < count; ++i) {
+    const tt_problem& p = probs[i];
+    first[i] = nj;
+    cnt[i] = 0;
+    hstat[i] = TT_OK;
+    const int d = p.d;
+    int stv = TT_OK;
+    if (d < 1 || d > o.max_d || p.n_grid < 2 || p.n_grid > o.max_n || p.max_rank < 1 ||
+        p.max_rank > o.max_rank || !p.spot || !p.cov || !p.damping ||
+        (p.payoff != TT_MIN_CALL && p.payoff != TT_MAX_CALL))
+      stv = (d > o.max_d || p.n_grid > o.max_n || p.max_rank > o.max_rank) ? TT_ERR_CAPACITY
+                                                                             : TT_ERR_INVALID;
+    else if (!(p.trunc_L > 0) || !std::isfinite(p.trunc_L) || !(p.maturity > 0) ||
+             !std::isfinite(p.maturity) || !(p.strike > 0) || !std::isfinite(p.strike) ||
+             !std::isfinite(p.rate) || !finite_all(p.spot, d) || !finite_all(p.cov, d * d) ||
+             !finite_all(p.damping, d))
+      stv = TT_ERR_INVALID;
+    else {
+      for (int j = 0; j < d; ++j)
+        if (!(p.spot[j] > 0)) stv = TT_ERR_INVALID;
+      if (stv == TT_OK && !cholesky_ok(p.cov, d)) stv = TT_ERR_NOT_PD;
+      if (stv == TT_OK) {
+        if (p.payoff == TT_MIN_CALL) {
+          double sd = 0.0;
+          for (int j = 0; j < d; ++j) {
+            if (!(-p.damping[j] > 0)) stv = TT_ERR_STRIP;
+            sd += -p.damping[j];
+          }
+          if (!(sd > 1.0)) stv = TT_ERR_STRIP;
+        } else {
+          for (int j = 0; j < d; ++j)
+            if (!(std::fabs(p.damping[j]) > 0)) stv = TT_ERR_STRIP;
+        }
+      }
+    }
+    if (stv != TT_OK) {
+      hstat[i] = stv;
+      continue;
+    }
+    const double T = p.maturity, K = p.strike, lk = std::log(K);
+    const int N = p.n_grid;
+    const double eta = 2.0 * p.trunc_L / N;
+    const double weight = std::exp(-p.rate * T) * std::pow(eta / (2.0 * M_PI), d);
+    std::vector<double> m(d);
+    for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
+    const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
+    for (int term = 0; term < terms; ++term) {
+      JobDesc jd;
+      std::memset(&jd, 0, sizeof(jd));
+      jd.d = d;
+      jd.n = N;
+      jd.rmax = p.max_rank;
+      jd.instance = i;
+      jd.term = term;
+      jd.param_off = (int)poff;
+      jd.seed = p.seed;
+      jd.T = T;
+      jd.L = p.trunc_L;
+      jd.weight = weight;
+      double* cv = params + poff;
+      double* dl = cv + (size_t)d * d;
+      double* pc = dl + d;
+      double* kd = pc + d;
+      poff += (size_t)d * d + 3 * (size_t)d;
+      if (p.payoff == TT_MIN_CALL) {
+        std::memcpy(cv, p.cov, sizeof(double) * d * d);
+        double sd = 0.0, dm = 0.0, quad = 0.0;
+        for (int j = 0; j < d; ++j) {
+          dl[j] = -p.damping[j];
+          sd += dl[j];
+          dm += dl[j] * m[j];
+          kd[j] = 0.0;
+        }
+        for (int j = 0; j < d; ++j) {
+          double cd = 0.0;
+          for (int l = 0; l < d; ++l) cd += p.cov[j * d + l] * dl[l];
+          pc[j] = m[j] + T * cd;
+          quad += dl[j] * cd;
+        }
+        jd.cauchy = 1;
+        jd.D0 = 1.0 - sd;
+        jd.logscale = lk + dm + 0.5 * T * quad;
+        jd.sign = (d % 2 == 1) ? 1.0 : -1.0;  // (-1)^(d+1)
+      } else {
+        // term `term`: y_term = x_term, y_l = x_l - x_term; C' = A Cov A^T
+        const int j0 = term;
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) {
+            auto cov = [&](int r, int c) { return p.cov[r * d + c]; };
+            double v = cov(a, b);
+            if (a != j0) v -= cov(j0, b);
+            if (b != j0) v -= cov(a, j0);
+            if (a != j0 && b != j0) v += cov(j0, j0);
+            cv[a * d + b] = v;
+          }
+        double lsc = lk, quad = 0.0;
+        for (int l = 0; l < d; ++l) {
+          dl[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
+          kd[l] = l == j0 ? 1.0 : 0.0;
+        }
+        for (int l = 0; l < d; ++l) {
+          const double mp = l == j0 ? m[j0] : m[l] - m[j0];
+          double cd = 0.0;
+          for (int q = 0; q < d; ++q) cd += cv[l * d + q] * dl[q];
+          pc[l] = mp + T * cd;
+          lsc += dl[l] * mp;
+          quad += dl[l] * cd;
+        }
+        jd.cauchy = 0;
+        jd.D0 = 0.0;
+        jd.logscale = lsc + 0.5 * T * quad;
+        jd.sign = 1.0;
+      }
+      jobs[nj] = jd;
+      cost.push_back((double)std::max(d - 1, 1) * N * (double)p.max_rank * p.max_rank * (d > 1 ? 1.0 : 0.01));
+      ++nj;
+      ++cnt[i];
+    }
+  }
+  for (int j = 0; j < nj; ++j) order[j] = j;
+  std::stable_sort(order, order + nj, [&](int a, int b) { return cost[a] > cost[b]; });
+  h->count = count;
+  h->njobs = nj;
+  // pack the used parts into one contiguous block: one host-to-device copy
+  size_t off = 0;
+  auto put = [&](size_t src_off, size_t bytes) {
+    const size_t at = off;
+    if (bytes) std::memcpy(h->h_pack + at, h->h_stage + src_off, bytes);
+    off = align_up(off + bytes, 16);
+    return at;
+  };
+  h->p_jobs = put(h->dl.o_jobs, sizeof(JobDesc) * nj);
+  h->p_params = put(h->dl.o_params, sizeof(double) * poff);
+  h->p_order = put(h->dl.o_order, sizeof(int) * nj);
+  h->p_first = put(h->dl.o_first, sizeof(int) * count);
+  h->p_count = put(h->dl.o_count, sizeof(int) * count);
+  h->p_hstatus = put(h->dl.o_hstatus, sizeof(int) * count);
+  h->p_bytes = off;
+  h->last_h2d = off;
+  if (off && cudaMemcpyAsync(h->ws + h->dl.stage, h->h_pack, off, cudaMemcpyHostToDevice,
+                             h->stream) != cudaSuccess)
+    return TT_ERR_CUDA;
+  return TT_OK;
+}
+
+int run_impl(tt_pricer* h) {
+  char* st = h->ws + h->dl.stage;
+  const JobDesc* jobs = reinterpret_cast<const JobDesc*>(st + h->p_jobs);
+  const double* params = reinterpret_cast<const double*>(st + h->p_params);
+  const int* order = reinterpret_cast<const int*>(st + h->p_order);
+  const int* first = reinterpret_cast<const int*>(st + h->p_first);
+  const int* cnt = reinterpret_cast<const int*>(st + h->p_count);
+  const int* hstat = reinterpret_cast<const int*>(st + h->p_hstatus);
+  int* counter = reinterpret_cast<int*>(h->ws + h->dl.counter);
+  JobResult* jres = reinterpret_cast<JobResult*>(h->ws + h->dl.jres);
+  InstanceResult* ires = reinterpret_cast<InstanceResult*>(h->ws + h->dl.ires);
+  char* scratch = h->ws + h->dl.scratch;
+  if (cudaMemsetAsync(counter, 0, sizeof(int), h->stream) != cudaSuccess) return TT_ERR_CUDA;
+  if (h->njobs > 0) {
+    const int grid = std::min(h->grid, h->njobs);
+    if (h->R.o.precision == TT_FP64)
+      ttp::tt_cross_kernel<double><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
+    else
+      ttp::tt_cross_kernel<float><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
+    if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
+  }
+  if (h->count > 0) {
+    ttp::finalize_kernel<<<(h->count + 127) / 128, 128, 0, h->stream>>>(jobs, jres, first, cnt, hstat,
+                                                                          h->count, ires);
+    if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
+  }
+  return TT_OK;
+}
+
+int results_impl(tt_pricer* h, double* prices, tt_diag* diag) {
+  if (h->count > 0 && !prices) return TT_ERR_INVALID;
+  h->last_d2h = sizeof(InstanceResult) * (size_t)h->count;
+  if (h->count > 0) {
+    if (cudaMemcpyAsync(h->h_ires, h->ws + h->dl.ires, h->last_d2h, cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+      return TT_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TT_ERR_CUDA;
+  int worst_err = 0, worst_warn = 0;
+  for (int i = 0; i < h->count; ++i) {
+    const InstanceResult& r = h->h_ires[i];
+    prices[i] = r.price;
+    if (diag) {
+      diag[i].status = r.status;
+      diag[i].half_sweeps = r.half_sweeps;
+      diag[i].final_rank_max = r.max_rank;
+      diag[i].terms = r.terms;
+      diag[i].evaluations = r.evaluations;
+      diag[i].imag_part = r.imag;
+      diag[i].flops = r.flops;
+    }
+    if (r.status < 0 && (worst_err == 0 || r.status < worst_err)) worst_err = r.status;
+    if (r.status > worst_warn) worst_warn = r.status;
+  }
+  return worst_err != 0 ? worst_err : worst_warn;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tt_workspace_bytes(const tt_options* opt) {
+  Resolved R;
+  if (!resolve(opt, &R)) return 0;
+  const bool f64 = R.o.precision == TT_FP64;
+  SmemLayout S = make_smem(R.o, f64);
+  if (S.total > 227 * 1024) return 0;
+  int grid = 0;
+  if (cudaSetDevice(R.o.device) != cudaSuccess) return 0;
+  if (grid_for(R.o, S, &grid) != TT_OK) return 0;
+  Layout L = make_layout(R.o, f64);
+  return make_dev_layout(R, L, grid).total;
+}
+
+int tt_price_create(const tt_options* opt, tt_pricer** out) {
+  if (!out) return TT_ERR_INVALID;
+  *out = nullptr;
+  Resolved R;
+  if (!resolve(opt, &R)) return TT_ERR_INVALID;
+  const bool f64 = R.o.precision == TT_FP64;
+  SmemLayout S = make_smem(R.o, f64);
+  if (S.total > 227 * 1024) return TT_ERR_CAPACITY;
+  if (cudaSetDevice(R.o.device) != cudaSuccess) return TT_ERR_CUDA;
+  int grid = 0;
+  int rc = grid_for(R.o, S, &grid);
+  if (rc != TT_OK) return rc;
+  tt_pricer* h = new (std::nothrow) tt_pricer();
+  if (!h) return TT_ERR_INVALID;
+  h->R = R;
+  h->lay = make_layout(R.o, f64);
+  h->sml = S;
+  h->grid = grid;
+  h->dl = make_dev_layout(R, h->lay, grid);
+  h->stream = reinterpret_cast<cudaStream_t>(R.o.cuda_stream);
+  h->count = 0;
+  h->njobs = 0;
+  if (R.o.workspace) {
+    if (R.o.workspace_bytes < h->dl.total || (reinterpret_cast<uintptr_t>(R.o.workspace) & 255u)) {
+      delete h;
+      return TT_ERR_CAPACITY;
+    }
+    h->ws = reinterpret_cast<char*>(R.o.workspace);
+    h->own_ws = false;
+  } else {
+    if (cudaMalloc(&h->ws, h->dl.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return TT_ERR_CUDA;
+    }
+    h->own_ws = true;
+  }
+  h->h_stage = nullptr;
+  h->h_pack = nullptr;
+  h->h_ires = nullptr;
+  h->p_jobs = h->p_params = h->p_order = h->p_first = h->p_count = h->p_hstatus = h->p_bytes = 0;
+  h->last_h2d = h->last_d2h = 0;
+  if (cudaMallocHost(&h->h_stage, h->dl.stage_bytes) != cudaSuccess ||
+      cudaMallocHost(&h->h_pack, h->dl.stage_bytes) != cudaSuccess ||
+      cudaMallocHost(&h->h_ires, sizeof(InstanceResult) * R.o.max_batch) != cudaSuccess) {
+    cudaGetLastError();
+    tt_price_destroy(h);
+    return TT_ERR_CUDA;
+  }
+  std::memset(h->h_stage, 0, h->dl.stage_bytes);
+  *out = h;
+  return TT_OK;
+}
+
+int tt_price_prepare(tt_pricer* h, const tt_problem* probs, int count) {
+  if (!h) return TT_ERR_INVALID;
+  if (cudaSetDevice(h->R.o.device) != cudaSuccess) return TT_ERR_CUDA;
+  return prepare_impl(h, probs, count);
+}
+
+int tt_price_run(tt_pricer* h) {
+  if (!h) return TT_ERR_INVALID;
+  if (cudaSetDevice(h->R.o.device) != cudaSuccess) return TT_ERR_CUDA;
+  return run_impl(h);
+}
+
+int tt_price_results(tt_pricer* h, double* prices, tt_diag* diag) {
+  if (!h) return TT_ERR_INVALID;
+  if (cudaSetDevice(h->R.o.device) != cudaSuccess) return TT_ERR_CUDA;
+  return results_impl(h, prices, diag);
+}
+
+int tt_price_evaluate(tt_pricer* h, const tt_problem* probs, int count, double* prices,
+                      tt_diag* diag) {
+  if (!h) return TT_ERR_INVALID;
+  int rc = tt_price_prepare(h, probs, count);
+  if (rc != TT_OK) return rc;
+  rc = tt_price_run(h);
+  if (rc != TT_OK) return rc;
+  return tt_price_results(h, prices, diag);
+}
+
+void tt_price_destroy(tt_pricer* h) {
+  if (!h) return;
+  cudaSetDevice(h->R.o.device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
+  if (h->h_pack) cudaFreeHost(h->h_pack);
+  if (h->h_ires) cudaFreeHost(h->h_ires);
+  delete h;
+}
+
+int tt_price_transfer_bytes(const tt_pricer* h, size_t* h2d, size_t* d2h) {
+  if (!h) return TT_ERR_INVALID;
+  if (h2d) *h2d = h->last_h2d;
+  if (d2h) *d2h = h->last_d2h;
+  return TT_OK;
+}
+
+const char* tt_status_string(int status) {
+  switch (status) {
+    case TT_OK: return "ok";
+    case TT_WARN_NOT_CONVERGED: return "sweep cap reached before the price settled";
+    case TT_ERR_INVALID: return "invalid argument";
+    case TT_ERR_NOT_PD: return "covariance is not positive definite";
+    case TT_ERR_STRIP: return "damping outside the payoff transform's strip";
+    case TT_ERR_CAPACITY: return "exceeds the pricer's capacity";
+    case TT_ERR_CUDA: return "CUDA error";
+    case TT_ERR_NUMERIC: return "numerical failure (rank collapse or non-finite price)";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,664 @@
+// Device steps of one TT-cross job.  See ttprice_kernels.cuh for the overview.
+#pragma once
+
+#include <climits>
+
+#include "ttprice_kernels.cuh"
+
+namespace ttp {
+
+enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3 };
+enum : int { DIR_LR = 0, DIR_RL = 1 };
+
+// block sum of a complex double held by every thread; result valid in all threads
+__device__ __forceinline__ double2 block_sum_d2(double2 v, double* dscr) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    dscr[2 * warp] = v.x;
+    dscr[2 * warp + 1] = v.y;
+  }
+  __syncthreads();
+  double2 s = make_double2(0.0, 0.0);
+  for (int w = 0; w < kWarps; ++w) {
+    s.x += dscr[2 * w];
+    s.y += dscr[2 * w + 1];
+  }
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// job set-up: per-axis tables (FP64), their normalisation, initial right sets
+// ---------------------------------------------------------------------------
+// For axis j and grid point u the separable factor is
+//   kind 0:  1/(i u - delta_j)                       * e^{-i p_j u}
+//   kind 1:  1/((i u - delta_j)(1 - delta_j + i u))  * e^{-i p_j u}
+// stored as log|.| (minus its maximum over the grid) and a unit phase.
+template <typename R>
+__device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, double* dscr,
+                          double& norm_sum) {
+  const int d = jd.d, n = jd.n, tid = threadIdx.x;
+  const double* delta = prm + d * d;
+  const double* pcoef = delta + d;
+  const double* kind = pcoef + d;
+  const double eta = 2.0 * jd.L / n;
+  for (int i = tid; i < n; i += kThreads) x.u[i] = -jd.L + (i + 0.5) * eta;
+  for (int idx = tid; idx < d * n; idx += kThreads) {
+    const int j = idx / n, i = idx % n;
+    const double u = -jd.L + (i + 0.5) * eta;
+    const double dl = delta[j];
+    double lr = -0.5 * log(u * u + dl * dl);
+    double ph = -pcoef[j] * u - atan2(u, -dl);
+    if (kind[j] != 0.0) {
+      const double e = 1.0 - dl;
+      lr += -0.5 * log(u * u + e * e);
+      ph -= atan2(u, e);
+    }
+    double s, c;
+    sincos(ph, &s, &c);
+    x.lam[(size_t)j * x.nmax + i] = lr;
+    x.om[(size_t)j * x.nmax + i] = make_double2(c, s);
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  double part = 0.0;
+  for (int j = warp; j < d; j += kWarps) {
+    double mx = -1e300;
+    for (int i = lane; i < n; i += 32) mx = fmax(mx, x.lam[(size_t)j * x.nmax + i]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    for (int i = lane; i < n; i += 32) x.lam[(size_t)j * x.nmax + i] -= mx;
+    part += mx;  // identical in every lane
+  }
+  if (lane == 0) dscr[16 + warp] = part;
+  // initial right index sets, one thread per bond
+  for (int k = 1 + tid; k < d; k += kThreads) {
+    const int width = d - k;
+    const long long cap = jd.rmax;
+    long long rk = ipow_cap(n, k, cap + 1);
+    rk = rk < cap ? rk : cap;
+    const long long nw = ipow_cap(n, width, cap + 1);
+    if (nw < rk) rk = nw;
+    x.rsz[k] = (int)rk;
+    if (nw == rk) {  // every right multi-index, lexicographic
+      for (int b = 0; b < rk; ++b) {
+        uint16_t* dst = rset_at(x, k, b);
+        int rem = b;
+        for (int pos = width - 1; pos >= 0; --pos) {
+          dst[pos] = (uint16_t)(rem % n);
+          rem /= n;
+        }
+      }
+    } else {
+      uint16_t* c0 = rset_at(x, k, 0);
+      for (int pos = 0; pos < width; ++pos) c0[pos] = (uint16_t)(n / 2);
+      for (int b = 1; b < rk; ++b) {
+        uint16_t* dst = rset_at(x, k, b);
+        bool fresh = false;
+        for (int t = 0; t < 65536 && !fresh; ++t) {
+          for (int pos = 0; pos < width; ++pos)
+            dst[pos] = (uint16_t)(splitmix64(pivot_key(jd.seed, jd.term, k, t, b, k + pos)) % n);
+          fresh = true;
+          for (int bb = 0; bb < b && fresh; ++bb) {
+            const uint16_t* o = rset_at(x, k, bb);
+            bool same = true;
+            for (int pos = 0; pos < width && same; ++pos) same = (o[pos] == dst[pos]);
+            fresh = !same;
+          }
+        }
+        if (!fresh) x.misc[MISC_DRAW] = 1;
+      }
+    }
+  }
+  if (tid == 0) {
+    x.lsz[0] = 1;
+    x.rsz[d] = 1;
+  }
+  __syncthreads();
+  norm_sum = 0.0;
+  for (int w = 0; w < kWarps; ++w) norm_sum += dscr[16 + w];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// per-core states and the pair table (FP64, stored in R)
+// ---------------------------------------------------------------------------
+// Left entry a (axes 0..k-1) and right entry b (axes k+1..d-1) of core k:
+//   E0(a,b) = lam_L + lam_R - T/2 (q_L + q_R + 2 u_L^T Cov_LR u_R)
+//   H(a,b)  = -T (Cov_kL u_L + Cov_kR u_R)      (coefficient of u at axis k)
+//   S0(a,b) = sum u_L + sum u_R,   Om(a,b) = phase_L * phase_R
+// so that at grid point u of axis k the log-magnitude is
+//   E0 + lam_k(u) - T/2 Cov_kk u^2 + H u.
+template <typename R>
+__device__ void core_states(Ctx<R>& x, int k, int dir) {
+  const int d = x.d, tid = threadIdx.x;
+  const int nl = x.lsz[k], nr = x.rsz[k + 1];
+  const int wr = d - k - 1;
+  const double* C = x.cov;
+  for (int a = tid; a < nl; a += kThreads) {
+    const uint16_t* ix = lset_at(x, k, a);
+    double q = 0.0, s = 0.0, lm = 0.0, y = 0.0;
+    double2 om = make_double2(1.0, 0.0);
+    for (int j = 0; j < k; ++j) {
+      const double uj = x.u[ix[j]];
+      double t = 0.0;
+      for (int l = 0; l < k; ++l) t += C[j * d + l] * x.u[ix[l]];
+      q += uj * t;
+      s += uj;
+      lm += x.lam[(size_t)j * x.nmax + ix[j]];
+      const double2 w = x.om[(size_t)j * x.nmax + ix[j]];
+      om = make_double2(om.x * w.x - om.y * w.y, om.x * w.y + om.y * w.x);
+      y += C[k * d + j] * uj;
+    }
+    for (int l = 0; l < wr; ++l) {
+      double v = 0.0;
+      for (int j = 0; j < k; ++j) v += C[(k + 1 + l) * d + j] * x.u[ix[j]];
+      x.lvec[(size_t)a * x.dmax + l] = v;
+    }
+    double* st = x.lstate + 8 * a;
+    st[0] = q; st[1] = s; st[2] = lm; st[3] = y; st[4] = om.x; st[5] = om.y;
+  }
+  for (int b = tid; b < nr; b += kThreads) {
+    const uint16_t* ix = rset_at(x, k + 1, b);
+    double q = 0.0, s = 0.0, lm = 0.0, z = 0.0;
+    double2 om = make_double2(1.0, 0.0);
+    for (int l = 0; l < wr; ++l) {
+      const int ax = k + 1 + l;
+      const double ul = x.u[ix[l]];
+      double t = 0.0;
+      for (int mm = 0; mm < wr; ++mm) t += C[ax * d + k + 1 + mm] * x.u[ix[mm]];
+      q += ul * t;
+      s += ul;
+      lm += x.lam[(size_t)ax * x.nmax + ix[l]];
+      const double2 w = x.om[(size_t)ax * x.nmax + ix[l]];
+      om = make_double2(om.x * w.x - om.y * w.y, om.x * w.y + om.y * w.x);
+      z += C[k * d + ax] * ul;
+      x.rvec[(size_t)b * x.dmax + l] = ul;
+    }
+    double* st = x.rstate + 8 * b;
+    st[0] = q; st[1] = s; st[2] = lm; st[3] = z; st[4] = om.x; st[5] = om.y;
+  }
+  __syncthreads();
+  const double T = x.T, ls = Num<R>::kLogScale;
+  for (int p = tid; p < nl * nr; p += kThreads) {
+    const int a = p % nl, b = p / nl;
+    const double* sl = x.lstate + 8 * a;
+    const double* sr = x.rstate + 8 * b;
+    double xab = 0.0;
+    for (int l = 0; l < wr; ++l) xab += x.lvec[(size_t)a * x.dmax + l] * x.rvec[(size_t)b * x.dmax + l];
+    const double e0 = sl[2] + sr[2] - 0.5 * T * (sl[0] + sr[0] + 2.0 * xab);
+    const double h = -T * (sl[3] + sr[3]);
+    const double s0 = sl[1] + sr[1];
+    const double ore = sl[4] * sr[4] - sl[5] * sr[5];
+    const double oim = sl[4] * sr[5] + sl[5] * sr[4];
+    const int o = dir == DIR_LR ? a : b, c = dir == DIR_LR ? b : a;
+    const int idx = o * x.rall + c;
+    x.pE0[idx] = (R)(e0 * ls);
+    x.pH[idx] = (R)(h * ls);
+    x.pS0[idx] = (R)s0;
+    x.pOre[idx] = (R)ore;
+    x.pOim[idx] = (R)oim;
+  }
+  __syncthreads();
+}
+
+// the active axis' table in shared memory (R precision, exponent pre-scaled)
+template <typename R>
+__device__ void load_axis_table(Ctx<R>& x, int k) {
+  const double ckk = x.cov[k * x.d + k], T = x.T, ls = Num<R>::kLogScale;
+  for (int i = threadIdx.x; i < x.n; i += kThreads) {
+    const double u = x.u[i];
+    x.tl[i] = (R)((x.lam[(size_t)k * x.nmax + i] - 0.5 * T * ckk * u * u) * ls);
+    x.tu[i] = (R)u;
+    const double2 w = x.om[(size_t)k * x.nmax + i];
+    x.tor[i] = (R)w.x;
+    x.toi[i] = (R)w.y;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// GEPP on the candidate matrix sw (q rows x ncol, column-major, leading dim ld)
+// Returns the number of pivots; selr/selc hold (candidate row, column) pairs.
+// Each thread owns one candidate row (q <= kThreads).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  cpx<R>* S = x.sw;
+  for (int c = warp; c < ncol; c += kWarps) {
+    R mx = 0;
+    for (int r = lane; r < q; r += 32) mx = fmax(mx, cabs2(S[c * ld + r]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) x.colmax[c] = mx;
+  }
+  __syncthreads();
+  const bool own = tid < q;
+  bool mine_used = false;
+  R v = own ? cabs2(S[tid]) : R(-1);
+  int vi = own ? tid : INT_MAX;
+  int buf = 0;
+  block_argmax(v, vi, x.redv, x.redi, buf);
+  int nsel = 0;
+  double fl = 0.0;
+  for (int c = 0; c < ncol; ++c) {
+    const int p = vi;
+    const bool take = (v > thr2 * x.colmax[c]) && (v > R(0));
+    if (take) {
+      if (tid == 0) {
+        x.selr[nsel] = p;
+        x.selc[nsel] = c;
+      }
+      const bool active = own && !mine_used && tid != p;
+      if (tid == p) mine_used = true;
+      if (active && c + 1 < ncol) {
+        const cpx<R> l = cmul(S[c * ld + tid], crecip(S[c * ld + p]));
+        for (int j = c + 1; j < ncol; ++j) cfms(S[j * ld + tid], l, S[j * ld + p]);
+      }
+      ++nsel;
+      fl += 8.0 * (double)(q - nsel) * (double)(ncol - c - 1);
+    }
+    if (c + 1 < ncol) {
+      const bool active = own && !mine_used;
+      v = active ? cabs2(S[(c + 1) * ld + tid]) : R(-1);
+      vi = active ? tid : INT_MAX;
+      buf ^= 1;
+      block_argmax(v, vi, x.redv, x.redi, buf);
+    }
+  }
+  if (tid == 0) x.flops += fl;
+  __syncthreads();
+  return nsel;
+}
+
+// ---------------------------------------------------------------------------
+// M = P^{-1} by Gauss-Jordan with partial pivoting, in R, scratch in sw
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void invert_pivots(Ctx<R>& x, int rho) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ld = 2 * rho;
+  cpx<R>* G = x.sw;
+  for (int idx = tid; idx < rho * rho; idx += kThreads) {
+    const int r = idx / rho, c = idx % rho;
+    G[r * ld + c] = x.P[r * x.rall + c];
+    G[r * ld + rho + c] = cpx<R>{R(r == c), R(0)};
+  }
+  __syncthreads();
+  for (int c = 0; c < rho; ++c) {
+    if (warp == 0) {
+      R v = R(-1);
+      int vi = INT_MAX;
+      for (int r = c + lane; r < rho; r += 32) am_merge(v, vi, cabs2(G[r * ld + c]), r);
+      warp_argmax(v, vi);
+      if (lane == 0) {
+        x.misc[MISC_PIV] = vi;
+        if (!(v > R(0))) x.misc[MISC_FAIL] = 1;
+      }
+    }
+    __syncthreads();
+    const int p = x.misc[MISC_PIV];
+    if (p != c && p < rho) {
+      for (int j = tid; j < ld; j += kThreads) {
+        const cpx<R> t = G[c * ld + j];
+        G[c * ld + j] = G[p * ld + j];
+        G[p * ld + j] = t;
+      }
+    }
+    __syncthreads();
+    const cpx<R> inv = crecip(G[c * ld + c]);
+    for (int r = tid; r < rho; r += kThreads) x.swcol[r] = G[r * ld + c];
+    for (int j = tid; j < ld; j += kThreads) x.swrow[j] = cmul(G[c * ld + j], inv);
+    __syncthreads();
+    for (int idx = tid; idx < rho * ld; idx += kThreads) {
+      const int r = idx / ld, j = idx % ld;
+      if (r == c) {
+        G[idx] = x.swrow[j];
+      } else {
+        cfms(G[idx], x.swcol[r], x.swrow[j]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < rho * rho; idx += kThreads) {
+    const int r = idx / rho, c = idx % rho;
+    x.M[r * x.rall + c] = G[r * ld + rho + c];
+  }
+  if (tid == 0) x.flops += 8.0 * (double)rho * rho * (2.0 * rho);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// evaluate pivot row j of P (fiber row g at the kept columns)
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void eval_prow(Ctx<R>& x, int j, int g, int rho) {
+  const int o = g / x.n, i = g % x.n;
+  for (int t = threadIdx.x; t < rho; t += kThreads) x.P[j * x.rall + t] = eval_point(x, o, i, x.jp[t]);
+}
+
+// ---------------------------------------------------------------------------
+// one core of a half-sweep: tournament, maxvol, interpolation solve
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
+  const int tid = threadIdx.x;
+  const int N = x.n;
+  core_states(x, k, dir);
+  load_axis_table(x, k);
+  const int no = dir == DIR_LR ? x.lsz[k] : x.rsz[k + 1];
+  const int nc = dir == DIR_LR ? x.rsz[k + 1] : x.lsz[k];
+  const int m = no * N;
+  const int b = kn.block_rows;
+  const int nb = (m + b - 1) / b;
+  const int ldq = x.rall + b;
+  const R thr2 = (R)(kn.theta * kn.theta);
+  if (tid == 0) x.evals += (long long)m * nc;
+
+  // ---- GEPP tournament over row blocks ----
+  int rho = 0;
+  for (int beta = 0; beta < nb; ++beta) {
+    const int rs = beta * b;
+    const int bs = min(b, m - rs);
+    const int q = rho + bs;
+    for (int idx = tid; idx < q * nc; idx += kThreads) {
+      const int r = idx % q, c = idx / q;
+      const int g = r < rho ? x.wrow[r] : rs + r - rho;
+      x.sw[c * ldq + r] = eval_point(x, g / N, g % N, c);
+    }
+    if (tid == 0) x.flops += 24.0 * q * nc;
+    __syncthreads();
+    const int nsel = gepp_select(x, q, nc, ldq, thr2);
+    for (int t = tid; t < nsel; t += kThreads) {
+      const int cr = x.selr[t];
+      x.wnew[t] = cr < rho ? x.wrow[cr] : rs + cr - rho;
+    }
+    __syncthreads();
+    for (int t = tid; t < nsel; t += kThreads) {
+      x.wrow[t] = x.wnew[t];
+      x.jp[t] = x.selc[t];
+    }
+    rho = nsel;
+    __syncthreads();
+  }
+  if (rho == 0) {
+    if (tid == 0) x.misc[MISC_FAIL] = 1;
+    __syncthreads();
+    return 0;
+  }
+
+  // ---- pivot rows and cyclic block maxvol on the kept columns ----
+  for (int idx = tid; idx < rho * rho; idx += kThreads) {
+    const int j = idx / rho, t = idx % rho;
+    const int g = x.wrow[j];
+    x.P[j * x.rall + t] = eval_point(x, g / N, g % N, x.jp[t]);
+  }
+  for (int idx = tid; idx < no * rho; idx += kThreads) {
+    const int o = idx / rho, t = idx % rho;
+    x.sacc[o * x.rall + t] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const R thr = (R)((1.0 + kn.tau) * (1.0 + kn.tau));
+  int quiet = 0, visits = 0, beta = 0;
+  bool mvalid = false;
+  int buf = 0;
+  const int nct = (rho + 3) / 4;
+  const int rtiles = kThreads / nct;  // row tiles per round
+  const int rpr = 4 * rtiles;
+  while (quiet < nb && visits < 4 * nb) {
+    if (!mvalid) {
+      invert_pivots(x, rho);
+      mvalid = true;
+    }
+    const int rs = beta * b;
+    const int bs = min(b, m - rs);
+    cpx<R>* A = x.sw;  // bs x rho, column-major, leading dimension b
+    for (int idx = tid; idx < bs * rho; idx += kThreads) {
+      const int r = idx % bs, t = idx / bs;
+      const int g = rs + r;
+      A[t * b + r] = eval_point(x, g / N, g % N, x.jp[t]);
+    }
+    if (tid == 0) x.flops += 24.0 * bs * rho + 8.0 * (double)bs * rho * rho;
+    __syncthreads();
+    if (visits < nb) {  // first pass: accumulate the fiber's row sums over i per outer index
+      const int olo = rs / N, ohi = (rs + bs - 1) / N;
+      const int nol = ohi - olo + 1;
+      for (int idx = tid; idx < nol * rho; idx += kThreads) {
+        const int ol = idx % nol, t = idx / nol;
+        const int o = olo + ol;
+        const int r0 = max(o * N, rs) - rs, r1 = min(o * N + N, rs + bs) - rs;
+        R sr = 0, si = 0, cr = 0, ci = 0;  // compensated (Kahan) sums
+        for (int r = r0; r < r1; ++r) {
+          const cpx<R> a = A[t * b + r];
+          R y = a.re - cr; R s2 = sr + y; cr = (s2 - sr) - y; sr = s2;
+          y = a.im - ci; s2 = si + y; ci = (s2 - si) - y; si = s2;
+        }
+        double2& acc = x.sacc[o * x.rall + t];
+        acc.x += (double)sr;
+        acc.y += (double)si;
+      }
+    }
+    // B = A M in row strips; every strip is read completely before it is overwritten
+    R bv = R(-1);
+    int bi = INT_MAX;
+    for (int r0 = 0; r0 < bs; r0 += rpr) {
+      const int rt = tid % rtiles, ct = tid / rtiles;
+      const int row0 = r0 + 4 * rt, col0 = 4 * ct;
+      const bool act = ct < nct && row0 < bs;
+      cpx<R> acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = cpx<R>{R(0), R(0)};
+      if (act) {
+        for (int t = 0; t < rho; ++t) {
+          cpx<R> av[4], mv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = (row0 + a < bs) ? A[t * b + row0 + a] : cpx<R>{R(0), R(0)};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            mv[c] = (col0 + c < rho) ? x.M[t * x.rall + col0 + c] : cpx<R>{R(0), R(0)};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cfma(acc[a][c], av[a], mv[c]);
+        }
+      }
+      __syncthreads();
+      if (act) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int r = row0 + a, cc = col0 + c;
+            if (r < bs && cc < rho) {
+              A[cc * b + r] = acc[a][c];
+              am_merge(bv, bi, cabs2(acc[a][c]), r * rho + cc);
+            }
+          }
+      }
+    }
+    buf ^= 1;
+    block_argmax(bv, bi, x.redv, x.redi, buf);
+    bool swapped = false;
+    for (int it = 0; it < rho; ++it) {
+      if (!(bv > thr)) break;
+      const int i = bi / rho, j = bi % rho;
+      for (int r = tid; r < bs; r += kThreads) x.swcol[r] = A[j * b + r];
+      for (int t = tid; t < rho; t += kThreads) x.swrow[t] = A[t * b + i];
+      if (tid == 0) x.wrow[j] = rs + i;
+      __syncthreads();
+      eval_prow(x, j, rs + i, rho);
+      const cpx<R> ipiv = crecip(x.swrow[j]);
+      bv = R(-1);
+      bi = INT_MAX;
+      for (int idx = tid; idx < bs * rho; idx += kThreads) {
+        const int r = idx % bs, t = idx / bs;
+        cpx<R> rv = x.swrow[t];
+        if (t == j) rv.re -= R(1);
+        cpx<R> bb = A[t * b + r];
+        cfms(bb, x.swcol[r], cmul(rv, ipiv));
+        A[t * b + r] = bb;
+        am_merge(bv, bi, cabs2(bb), r * rho + t);
+      }
+      if (tid == 0) x.flops += 8.0 * bs * rho + 24.0 * rho;
+      buf ^= 1;
+      block_argmax(bv, bi, x.redv, x.redi, buf);
+      swapped = true;
+      mvalid = false;
+    }
+    quiet = swapped ? 0 : quiet + 1;
+    ++visits;
+    beta = (beta + 1) % nb;
+    __syncthreads();
+  }
+
+  // ---- contraction step: v <- (v S) P^{-1}, FP64 (Gaussian elimination on P^T) ----
+  for (int t = tid; t < rho; t += kThreads) {
+    double2 y = make_double2(0.0, 0.0);
+    for (int o = 0; o < no; ++o) {
+      const double2 v = x.vchain[o], s = x.sacc[o * x.rall + t];
+      y.x += v.x * s.x - v.y * s.y;
+      y.y += v.x * s.y + v.y * s.x;
+    }
+    x.ychain[t] = y;
+  }
+  __syncthreads();
+  double2* G = reinterpret_cast<double2*>(x.sw);  // rho x (rho+1), row-major
+  const int lg = rho + 1;
+  for (int idx = tid; idx < rho * lg; idx += kThreads) {
+    const int r = idx / lg, c = idx % lg;
+    if (c < rho) {
+      const cpx<R> pv = x.P[c * x.rall + r];
+      G[idx] = make_double2((double)pv.re, (double)pv.im);
+    } else {
+      G[idx] = x.ychain[r];
+    }
+  }
+  __syncthreads();
+  double2* fac = reinterpret_cast<double2*>(x.swcol);
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int c = 0; c < rho; ++c) {
+    if (warp == 0) {
+      double v = -1.0;
+      int vi = INT_MAX;
+      for (int r = c + lane; r < rho; r += 32) {
+        const double2 g = G[r * lg + c];
+        am_merge(v, vi, g.x * g.x + g.y * g.y, r);
+      }
+      warp_argmax(v, vi);
+      if (lane == 0) {
+        x.misc[MISC_PIV] = vi;
+        if (!(v > 0.0)) x.misc[MISC_FAIL] = 1;
+      }
+    }
+    __syncthreads();
+    const int p = x.misc[MISC_PIV];
+    if (p != c && p < rho) {
+      for (int j = c + tid; j < lg; j += kThreads) {
+        const double2 t = G[c * lg + j];
+        G[c * lg + j] = G[p * lg + j];
+        G[p * lg + j] = t;
+      }
+    }
+    __syncthreads();
+    {
+      const double2 pv = G[c * lg + c];
+      const double den = pv.x * pv.x + pv.y * pv.y;
+      for (int r = c + 1 + tid; r < rho; r += kThreads) {
+        const double2 g = G[r * lg + c];
+        fac[r] = make_double2((g.x * pv.x + g.y * pv.y) / den, (g.y * pv.x - g.x * pv.y) / den);
+      }
+    }
+    __syncthreads();
+    const int w = lg - c - 1;
+    for (int idx = tid; idx < (rho - c - 1) * w; idx += kThreads) {
+      const int r = c + 1 + idx / w, j = c + 1 + idx % w;
+      const double2 f = fac[r], g = G[c * lg + j];
+      double2& t = G[r * lg + j];
+      t.x -= f.x * g.x - f.y * g.y;
+      t.y -= f.x * g.y + f.y * g.x;
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    for (int r = rho - 1; r >= 0; --r) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int j = r + 1 + lane; j < rho; j += 32) {
+        const double2 g = G[r * lg + j], v = x.vchain[j];
+        s.x += g.x * v.x - g.y * v.y;
+        s.y += g.x * v.y + g.y * v.x;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+      }
+      if (lane == 0) {
+        const double2 rhs = G[r * lg + rho], pv = G[r * lg + r];
+        const double nx = rhs.x - s.x, ny = rhs.y - s.y;
+        const double den = pv.x * pv.x + pv.y * pv.y;
+        x.vchain[r] = make_double2((nx * pv.x + ny * pv.y) / den, (ny * pv.x - nx * pv.y) / den);
+      }
+      __syncwarp();
+    }
+  }
+  if (tid == 0) x.flops += 8.0 * (double)no * rho + 8.0 * (double)rho * rho * rho / 3.0;
+  __syncthreads();
+
+  // ---- new index set ----
+  if (dir == DIR_LR) {
+    const int w = k + 1;
+    for (int idx = tid; idx < rho * w; idx += kThreads) {
+      const int t = idx / w, pos = idx % w;
+      const int g = x.wrow[t];
+      lset_at(x, k + 1, t)[pos] = pos < k ? lset_at(x, k, g / N)[pos] : (uint16_t)(g % N);
+    }
+    if (tid == 0) x.lsz[k + 1] = rho;
+  } else {
+    const int w = x.d - k;
+    for (int idx = tid; idx < rho * w; idx += kThreads) {
+      const int t = idx / w, pos = idx % w;
+      const int g = x.wrow[t];
+      rset_at(x, k, t)[pos] = pos == 0 ? (uint16_t)(g % N) : rset_at(x, k + 1, g / N)[pos - 1];
+    }
+    if (tid == 0) x.rsz[k] = rho;
+  }
+  __syncthreads();
+  return rho;
+}
+
+// end core of a half-sweep: est = sum_o v[o] * sum_i A[(o,i)]
+template <typename R>
+__device__ double2 core_sum(Ctx<R>& x, int k, int dir, double* dscr) {
+  const int tid = threadIdx.x, N = x.n;
+  core_states(x, k, dir);
+  load_axis_table(x, k);
+  const int no = dir == DIR_LR ? x.lsz[k] : x.rsz[k + 1];
+  double2 est = make_double2(0.0, 0.0);
+  for (int o = 0; o < no; ++o) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = tid; i < N; i += kThreads) {
+      const cpx<R> a = eval_point(x, o, i, 0);
+      s.x += (double)a.re;
+      s.y += (double)a.im;
+    }
+    s = block_sum_d2(s, dscr);
+    const double2 v = x.vchain[o];
+    est.x += v.x * s.x - v.y * s.y;
+    est.y += v.x * s.y + v.y * s.x;
+  }
+  if (tid == 0) {
+    x.evals += (long long)no * N;
+    x.flops += 24.0 * (double)no * N;
+  }
+  return est;
+}
+
+}  // namespace ttp

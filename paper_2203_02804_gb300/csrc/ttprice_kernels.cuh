@@ -1,0 +1,272 @@
+// Device side of the tensor-train Fourier pricer (arXiv 2203.02804), sm_103a.
+//
+// One persistent CTA runs one whole TT-cross job (one train: the min-call, or
+// one term of the max-call) at a time, taking jobs from a queue sorted by cost.
+// Every step of a core update is fused in the CTA and the fiber matrix never
+// leaves shared memory:
+//   (a) integrand evaluation on the fibers (Eq. main / Eq. discr integrand,
+//       written as exp(E) * unit phase * rational factor, with the quadratic
+//       form u^T Cov u split into per-index-set partial sums so that one point
+//       costs a few FMAs, one exp2 and one reciprocal);
+//   (b) cross-interpolation linear algebra (Section IV.B): GEPP tournament over
+//       row blocks for the initial rows, then cyclic block maxvol with block
+//       GEMMs B = A M and warp-shuffle argmax reductions;
+//   (c) the contraction with the quadrature weights (Section IV.A): the row sums
+//       of each core's fiber are accumulated while it streams through, and the
+//       running product v <- v S P^{-1} is an FP64 solve.
+// No wait in this file spins: every loop has a fixed or counted bound.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttp {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NUMERIC = -6, ST_INVALID = -1 };
+
+template <typename R>
+struct cpx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ void cfma(cpx<R>& acc, cpx<R> a, cpx<R> b) {  // acc += a*b
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+template <typename R>
+__device__ __forceinline__ void cfms(cpx<R>& acc, cpx<R> a, cpx<R> b) {  // acc -= a*b
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename R>
+__device__ __forceinline__ R cabs2(cpx<R> a) {
+  return a.re * a.re + a.im * a.im;
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> crecip(cpx<R> a) {
+  R s = R(1) / cabs2(a);
+  return {a.re * s, -a.im * s};
+}
+
+// exp of the log-magnitude: FP32 tables hold E in log2 units, FP64 in natural units.
+template <typename R> struct Num;
+template <> struct Num<float> {
+  static constexpr double kLogScale = 1.4426950408889634;  // log2(e)
+  __device__ static __forceinline__ float ex(float e) { return exp2f(e); }
+  __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+};
+template <> struct Num<double> {
+  static constexpr double kLogScale = 1.0;
+  __device__ static __forceinline__ double ex(double e) { return exp(e); }
+  __device__ static __forceinline__ double div(double a, double b) { return a / b; }
+};
+
+// ---------------------------------------------------------------------------
+// descriptors shared with the host
+// ---------------------------------------------------------------------------
+struct JobDesc {
+  int d, n, rmax, instance;
+  int cauchy;     // 1: min-call, has the 1/(D0 + i sum u) factor
+  int term;       // max-call term (0 for the min-call): selects the pivot stream
+  int param_off;  // doubles: cov[d*d] row-major, delta[d], pcoef[d], kind[d]
+  int pad;
+  unsigned long long seed;
+  double T, D0, L;
+  double logscale, sign, weight;  // true integrand = sign*exp(logscale + sum norms)*value
+};
+
+struct JobResult {
+  double est_re, est_im;  // TT sum of the normalised integrand
+  double norm_sum;        // sum over axes of the per-axis log normalisation
+  double flops;
+  long long evaluations;
+  int status, half_sweeps, max_rank, maxvol_capped;
+};
+
+struct InstanceResult {
+  double price, imag, flops;
+  long long evaluations;
+  int status, half_sweeps, max_rank, terms;
+};
+
+struct Knobs {
+  double theta;    // rank threshold
+  double tau;      // maxvol tolerance
+  double sweep_tol;
+  int max_half_sweeps;
+  int block_rows;
+};
+
+// per-CTA global scratch, byte offsets
+struct Layout {
+  size_t u, lam, om, lset, rset, lstate, rstate, lvec, rvec, pair, P, sacc, chain, stride;
+  int dmax, nmax, rmax;
+};
+
+// shared-memory carve, byte offsets (sizes depend on R)
+struct SmemLayout {
+  int sw, m, tab, colmax, wrow, wnew, jp, selr, selc, used, redv, redi, swcol, swrow, lsz, rsz,
+      misc, total;
+  int sw_elems;
+};
+
+// ---------------------------------------------------------------------------
+// block-wide argmax of (value, index): larger value wins, then lower index.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void am_merge(R& v, int& i, R v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void warp_argmax(R& v, int& i) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    R v2 = __shfl_xor_sync(0xffffffffu, v, off);
+    int i2 = __shfl_xor_sync(0xffffffffu, i, off);
+    am_merge(v, i, v2, i2);
+  }
+}
+// Writes the warp partial into buffer `buf`, syncs, and returns the block result
+// in every thread.  Callers alternate `buf` so that the next write cannot race
+// with slower warps still reading.
+template <typename R>
+__device__ __forceinline__ void block_argmax(R& v, int& i, R* redv, int* redi, int buf) {
+  warp_argmax(v, i);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    redv[buf * kWarps + warp] = v;
+    redi[buf * kWarps + warp] = i;
+  }
+  __syncthreads();
+  v = redv[buf * kWarps];
+  i = redi[buf * kWarps];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) am_merge(v, i, redv[buf * kWarps + w], redi[buf * kWarps + w]);
+}
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea and Flood 2014) as a counter-based hash
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long pivot_key(unsigned long long seed, int term, int k,
+                                                        int t, int b, int j) {
+  return seed ^ ((unsigned long long)term << 52) ^ ((unsigned long long)k << 40) ^
+         ((unsigned long long)t << 24) ^ ((unsigned long long)b << 12) ^ (unsigned long long)j;
+}
+// min(n^e, cap) without overflow
+__device__ __forceinline__ long long ipow_cap(long long n, int e, long long cap) {
+  long long v = 1;
+  for (int q = 0; q < e; ++q) {
+    v *= n;
+    if (v >= cap) return cap;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// per-CTA context
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Ctx {
+  // job
+  int d, n, rmax;
+  int cauchy;
+  R D0;
+  double T;
+  const double* cov;  // [d*d]
+  // global scratch
+  double* u;          // [n]
+  double* lam;        // [d][nmax]
+  double2* om;        // [d][nmax]
+  uint16_t* lset;     // [(dmax+1)][rmax_all][dmax]
+  uint16_t* rset;
+  double* lstate;     // [rmax_all][8]
+  double* rstate;
+  double* lvec;       // [rmax_all][dmax]
+  double* rvec;
+  R* pE0;
+  R* pH;
+  R* pS0;
+  R* pOre;
+  R* pOim;  // [rmax_all][rmax_all]
+  cpx<R>* P;          // [rmax_all][rmax_all] pivot rows A[W, Jp]
+  double2* sacc;      // [rmax_all][rmax_all]
+  double2* vchain;    // [rmax_all]
+  double2* ychain;    // [rmax_all]
+  int dmax, nmax, rall;
+  // shared
+  cpx<R>* sw;
+  cpx<R>* M;
+  R* tl;  // [nmax] lam' of the active axis (scaled)
+  R* tu;  // [nmax] u
+  R* tor;
+  R* toi;
+  R* colmax;
+  int* wrow;
+  int* wnew;
+  int* jp;
+  int* selr;
+  int* selc;
+  unsigned char* used;
+  R* redv;
+  int* redi;
+  cpx<R>* swcol;
+  cpx<R>* swrow;
+  int* lsz;
+  int* rsz;
+  int* misc;
+  // bookkeeping (thread 0 only)
+  double flops;
+  long long evals;
+};
+
+// Index sets: left set at bond k holds multi-indices over axes 0..k-1,
+// right set at bond k over axes k..d-1 (stored from position 0).
+template <typename R>
+__device__ __forceinline__ uint16_t* lset_at(const Ctx<R>& x, int k, int a) {
+  return x.lset + ((size_t)k * x.rall + a) * x.dmax;
+}
+template <typename R>
+__device__ __forceinline__ uint16_t* rset_at(const Ctx<R>& x, int k, int b) {
+  return x.rset + ((size_t)k * x.rall + b) * x.dmax;
+}
+
+// ---------------------------------------------------------------------------
+// integrand at one fiber point
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ cpx<R> eval_point(const Ctx<R>& x, int o, int i, int col) {
+  const int p = o * x.rall + col;
+  const R e = x.pE0[p] + x.tl[i] + x.pH[p] * x.tu[i];
+  cpx<R> w = cmul(cpx<R>{x.pOre[p], x.pOim[p]}, cpx<R>{x.tor[i], x.toi[i]});
+  R f = Num<R>::ex(e);
+  if (x.cauchy) {
+    const R s = x.pS0[p] + x.tu[i];
+    const R den = fma(s, s, x.D0 * x.D0);
+    f = Num<R>::div(f, den);
+    w = cmul(w, cpx<R>{x.D0, -s});
+  }
+  return {w.re * f, w.im * f};
+}
+
+}  // namespace ttp

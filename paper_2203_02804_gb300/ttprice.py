@@ -1,0 +1,226 @@
+"""Python binding of the C ABI in include/ttprice.h (ctypes; argument marshalling only).
+
+Every pricing step runs in libttprice.so's CUDA kernels.  PyTorch supplies the
+device workspace and the CUDA stream.  There is no CPU fallback: if the library
+is missing or CUDA is unavailable the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB
+
+TT_OK = 0
+TT_WARN_NOT_CONVERGED = 1
+TT_ERR_INVALID = -1
+TT_ERR_NOT_PD = -2
+TT_ERR_STRIP = -3
+TT_ERR_CAPACITY = -4
+TT_ERR_CUDA = -5
+TT_ERR_NUMERIC = -6
+
+TT_MIN_CALL = 0
+TT_MAX_CALL = 1
+TT_FP64 = 0
+TT_MIXED = 1
+
+EXPORTS = ("tt_price_create", "tt_workspace_bytes", "tt_price_evaluate", "tt_price_prepare",
+           "tt_price_run", "tt_price_results", "tt_price_transfer_bytes", "tt_price_destroy",
+           "tt_status_string")
+
+
+class tt_options(ctypes.Structure):
+    _fields_ = [("max_d", ctypes.c_int), ("max_n", ctypes.c_int), ("max_rank", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_half_sweeps", ctypes.c_int), ("sweep_tol", ctypes.c_double),
+                ("rank_tol", ctypes.c_double), ("maxvol_tol", ctypes.c_double),
+                ("block_rows", ctypes.c_int), ("device", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class tt_problem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("spot", ctypes.POINTER(ctypes.c_double)),
+                ("cov", ctypes.POINTER(ctypes.c_double)), ("rate", ctypes.c_double),
+                ("maturity", ctypes.c_double), ("strike", ctypes.c_double),
+                ("payoff", ctypes.c_int), ("damping", ctypes.POINTER(ctypes.c_double)),
+                ("n_grid", ctypes.c_int), ("trunc_L", ctypes.c_double),
+                ("max_rank", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+
+
+class tt_diag(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("half_sweeps", ctypes.c_int),
+                ("final_rank_max", ctypes.c_int), ("terms", ctypes.c_int),
+                ("evaluations", ctypes.c_longlong), ("imag_part", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libttprice.so (built by paper_2203_02804_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: run paper_2203_02804_gb300.build.build() first")
+    lib = ctypes.CDLL(p)
+    lib.tt_price_create.argtypes = [ctypes.POINTER(tt_options), ctypes.POINTER(ctypes.c_void_p)]
+    lib.tt_price_create.restype = ctypes.c_int
+    lib.tt_workspace_bytes.argtypes = [ctypes.POINTER(tt_options)]
+    lib.tt_workspace_bytes.restype = ctypes.c_size_t
+    lib.tt_price_evaluate.argtypes = [ctypes.c_void_p, ctypes.POINTER(tt_problem), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(tt_diag)]
+    lib.tt_price_evaluate.restype = ctypes.c_int
+    lib.tt_price_prepare.argtypes = [ctypes.c_void_p, ctypes.POINTER(tt_problem), ctypes.c_int]
+    lib.tt_price_prepare.restype = ctypes.c_int
+    lib.tt_price_run.argtypes = [ctypes.c_void_p]
+    lib.tt_price_run.restype = ctypes.c_int
+    lib.tt_price_results.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(tt_diag)]
+    lib.tt_price_results.restype = ctypes.c_int
+    lib.tt_price_transfer_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                                            ctypes.POINTER(ctypes.c_size_t)]
+    lib.tt_price_transfer_bytes.restype = ctypes.c_int
+    lib.tt_price_destroy.argtypes = [ctypes.c_void_p]
+    lib.tt_price_destroy.restype = None
+    lib.tt_status_string.argtypes = [ctypes.c_int]
+    lib.tt_status_string.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load_library().tt_status_string(int(code)).decode()
+
+
+@dataclass
+class Diag:
+    status: int
+    half_sweeps: int
+    final_rank_max: int
+    terms: int
+    evaluations: int
+    imag_part: float
+    flops: float
+
+
+class ProblemBatch:
+    """Host arrays of a batch, kept alive for the duration of the C calls."""
+
+    def __init__(self, problems: Sequence):
+        self.keep = []
+        self.arr = (tt_problem * max(1, len(problems)))()
+        dbl = ctypes.POINTER(ctypes.c_double)
+        for i, p in enumerate(problems):
+            spot = np.ascontiguousarray(p.spot, dtype=np.float64)
+            cov = np.ascontiguousarray(p.cov, dtype=np.float64)
+            damp = np.ascontiguousarray(p.damping, dtype=np.float64)
+            self.keep += [spot, cov, damp]
+            s = self.arr[i]
+            s.d = int(spot.size)
+            s.spot = spot.ctypes.data_as(dbl)
+            s.cov = cov.ctypes.data_as(dbl)
+            s.rate = float(p.rate)
+            s.maturity = float(p.maturity)
+            s.strike = float(p.strike)
+            s.payoff = TT_MIN_CALL if p.payoff == "min" else TT_MAX_CALL
+            s.damping = damp.ctypes.data_as(dbl)
+            s.n_grid = int(p.n_grid)
+            s.trunc_L = float(p.trunc_L)
+            s.max_rank = int(p.max_rank)
+            s.seed = int(p.seed) & ((1 << 64) - 1)
+        self.count = len(problems)
+
+
+class Pricer:
+    """Owns one tt_pricer handle on a CUDA device, with a torch-allocated workspace."""
+
+    def __init__(self, max_d: int, max_n: int, max_rank: int, max_batch: int,
+                 precision: str = "fp64", device: int = 0, stream=None, max_half_sweeps: int = 0,
+                 sweep_tol: float = 0.0, rank_tol: float = 0.0, maxvol_tol: float = 0.0,
+                 block_rows: int = 0, use_torch_workspace: bool = True):
+        import torch  # device memory and streams only
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the tensor-train pricer needs a CUDA device; none is available")
+        self.lib = load_library()
+        self.torch = torch
+        self.device = device
+        self.opts = tt_options()
+        o = self.opts
+        o.max_d, o.max_n, o.max_rank, o.max_batch = max_d, max_n, max_rank, max_batch
+        o.precision = TT_FP64 if precision == "fp64" else TT_MIXED
+        o.max_half_sweeps = max_half_sweeps
+        o.sweep_tol, o.rank_tol, o.maxvol_tol = sweep_tol, rank_tol, maxvol_tol
+        o.block_rows = block_rows
+        o.device = device
+        with torch.cuda.device(device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self.workspace = None
+        if use_torch_workspace:
+            nbytes = self.lib.tt_workspace_bytes(ctypes.byref(o))
+            if nbytes == 0:
+                raise ValueError("invalid pricer options (tt_workspace_bytes returned 0)")
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+            ptr = self.workspace.data_ptr()
+            o.workspace = ctypes.c_void_p((ptr + 255) // 256 * 256)
+            o.workspace_bytes = nbytes
+        h = ctypes.c_void_p()
+        rc = self.lib.tt_price_create(ctypes.byref(o), ctypes.byref(h))
+        if rc != TT_OK:
+            raise RuntimeError(f"tt_price_create failed: {status_string(rc)} ({rc})")
+        self.handle = h
+        self._batch = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tt_price_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- the C calls, one to one ---
+    def prepare(self, problems) -> int:
+        self._batch = ProblemBatch(problems)
+        return self.lib.tt_price_prepare(self.handle, self._batch.arr, self._batch.count)
+
+    def run(self) -> int:
+        return self.lib.tt_price_run(self.handle)
+
+    def results(self):
+        n = self._batch.count if self._batch else 0
+        prices = (ctypes.c_double * max(1, n))()
+        diags = (tt_diag * max(1, n))()
+        rc = self.lib.tt_price_results(self.handle, prices, diags)
+        return rc, np.array(prices[:n]), [Diag(*(getattr(d, f) for f, _ in tt_diag._fields_))
+                                          for d in diags[:n]]
+
+    def transfer_bytes(self):
+        """(host-to-device bytes of the last prepare, device-to-host bytes of the last results)."""
+        h2d, d2h = ctypes.c_size_t(), ctypes.c_size_t()
+        self.lib.tt_price_transfer_bytes(self.handle, ctypes.byref(h2d), ctypes.byref(d2h))
+        return int(h2d.value), int(d2h.value)
+
+    def evaluate(self, problems):
+        """Price a batch; returns (worst status, prices ndarray, list of Diag)."""
+        batch = ProblemBatch(problems)
+        n = batch.count
+        prices = (ctypes.c_double * max(1, n))()
+        diags = (tt_diag * max(1, n))()
+        rc = self.lib.tt_price_evaluate(self.handle, batch.arr, n, prices, diags)
+        return rc, np.array(prices[:n]), [Diag(*(getattr(d, f) for f, _ in tt_diag._fields_))
+                                          for d in diags[:n]]

@@ -1,0 +1,86 @@
+"""The C ABI on the CPU: the library builds for sm_103a, loads, exports every
+function include/ttprice.h declares, and the ctypes mirrors of its structs have
+the C layout (checked against gcc).  No compute call runs here."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2203_02804_gb300 import build, ttprice
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ttprice.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ttprice.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tt_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    assert set(names) == set(ttprice.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_without_gpu(lib):
+    assert lib.tt_status_string(0) == b"ok"
+    assert b"positive definite" in lib.tt_status_string(-2)
+
+
+def test_create_rejects_bad_options_without_touching_the_gpu(lib):
+    o = ttprice.tt_options()
+    o.max_d, o.max_n, o.max_rank, o.max_batch = 0, 64, 8, 1  # max_d < 1
+    h = ctypes.c_void_p()
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    assert not h.value
+    o.max_d, o.max_rank, o.block_rows = 4, 64, 250  # block_rows + max_rank > 256
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    lib.tt_price_destroy(None)
+
+
+def test_struct_layouts_match_c():
+    src = r"""
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "ttprice.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu\n", sizeof(tt_options), offsetof(tt_options, sweep_tol),
+             offsetof(tt_options, block_rows), offsetof(tt_options, cuda_stream),
+             offsetof(tt_options, workspace_bytes));
+      printf("%zu %zu %zu %zu %zu\n", sizeof(tt_problem), offsetof(tt_problem, rate),
+             offsetof(tt_problem, damping), offsetof(tt_problem, trunc_L), offsetof(tt_problem, seed));
+      printf("%zu %zu %zu\n", sizeof(tt_diag), offsetof(tt_diag, evaluations), offsetof(tt_diag, flops));
+      return 0;
+    }
+    """
+    with tempfile.TemporaryDirectory() as tmp:
+        c = os.path.join(tmp, "layout.c")
+        exe = os.path.join(tmp, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    T = ttprice
+    want = [
+        [ctypes.sizeof(T.tt_options), T.tt_options.sweep_tol.offset, T.tt_options.block_rows.offset,
+         T.tt_options.cuda_stream.offset, T.tt_options.workspace_bytes.offset],
+        [ctypes.sizeof(T.tt_problem), T.tt_problem.rate.offset, T.tt_problem.damping.offset,
+         T.tt_problem.trunc_L.offset, T.tt_problem.seed.offset],
+        [ctypes.sizeof(T.tt_diag), T.tt_diag.evaluations.offset, T.tt_diag.flops.offset],
+    ]
+    for line, w in zip(out, want):
+        assert [int(v) for v in line.split()] == w

@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+The oracle runs the same TT-cross reading (GEPP tournament, cyclic block
+maxvol, same seeds) in FP64 NumPy; in FP64 the GPU takes the same pivot
+decisions, so prices agree to the stated 1e-6 relative tolerance.  The mixed
+FP32 path is held to 1e-4 against the FP64 oracle.  Sizes span several row
+blocks and ragged tails; edge cases cover d = 1, full rank, exact low rank,
+invalid inputs and batching.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms, integrand, ttcross
+from paper_2203_02804_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-6
+MIXED_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def tp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_02804_gb300 import build, ttprice
+
+    build.build()
+    return ttprice
+
+
+def gpu_price(tp, problems, precision="fp64", **kw):
+    max_d = max(p.d for p in problems)
+    max_n = max(p.n_grid for p in problems)
+    max_r = max(p.max_rank for p in problems)
+    pr = tp.Pricer(max_d=max_d, max_n=max_n, max_rank=max_r, max_batch=len(problems),
+                   precision=precision, **kw)
+    rc, prices, diags = pr.evaluate(problems)
+    pr.close()
+    return rc, prices, diags
+
+
+def small_problem(d, n, r, payoff="min", seed=3, rho=0.3, trunc=20.0):
+    rng = np.random.default_rng(1000 + 17 * d + n + r)
+    spot = rng.uniform(90, 110, d)
+    sigma = rng.uniform(0.15, 0.35, d)
+    return inputs.Problem(spot=spot, cov=inputs.cov_from(sigma, inputs.equicorrelation(d, rho)),
+                          rate=0.02, maturity=1.0, strike=100.0, payoff=payoff,
+                          damping=np.full(d, -1.5), n_grid=n, trunc_L=trunc, max_rank=r, seed=seed)
+
+
+def oracle_price(p, precision="fp64"):
+    opts = ttcross.CrossOptions()
+    price, imag, diags = ttcross.tt_price(p, opts)
+    return price
+
+
+def test_two_asset_min_call_matches_oracle_tt(tp):
+    p = inputs.two_asset_min_call()
+    rc, prices, diags = gpu_price(tp, [p])
+    assert rc in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
+    ref = oracle_price(p)
+    assert abs(prices[0] / ref - 1) < FP64_TOL
+    assert diags[0].evaluations > 0 and diags[0].terms == 1
+
+
+@pytest.mark.parametrize("d,n,r", [(3, 16, 4), (3, 37, 6), (4, 13, 5), (3, 50, 8)])
+def test_small_min_calls_match_oracle(tp, d, n, r):
+    p = small_problem(d, n, r)
+    rc, prices, _ = gpu_price(tp, [p])
+    assert rc in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
+    assert abs(prices[0] / oracle_price(p) - 1) < FP64_TOL
+
+
+@pytest.mark.parametrize("d,n,r", [(2, 24, 6), (3, 20, 5)])
+def test_small_max_calls_match_oracle(tp, d, n, r):
+    p = small_problem(d, n, r, payoff="max")
+    rc, prices, diags = gpu_price(tp, [p])
+    assert rc in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
+    assert diags[0].terms == d
+    assert abs(prices[0] / oracle_price(p) - 1) < FP64_TOL
+
+
+def test_ragged_blocks_with_small_block_rows(tp):
+    """m = r*N = 8*50 = 400 rows in blocks of 64: six full blocks and a ragged tail of 16."""
+    p = small_problem(3, 50, 8)
+    rc, prices, _ = gpu_price(tp, [p], block_rows=64)
+    ref = ttcross.tt_price(p, ttcross.CrossOptions(block_rows=64))[0]
+    assert abs(prices[0] / ref - 1) < FP64_TOL
+
+
+def test_single_asset_is_the_grid_sum_and_black_scholes(tp):
+    p = inputs.Problem(spot=np.array([105.0]), cov=np.array([[0.0625]]), rate=0.03, maturity=0.8,
+                       strike=100.0, payoff="min", damping=np.array([-3.0]), n_grid=512,
+                       trunc_L=80.0, max_rank=4, seed=1)
+    rc, prices, diags = gpu_price(tp, [p])
+    assert rc == tp.TT_OK and diags[0].half_sweeps == 1
+    bs = closed_forms.bs_call(105.0, 100.0, 0.03, 0.8, 0.25)
+    assert abs(prices[0] / bs - 1) < 1e-10
+
+
+def test_full_rank_reproduces_full_grid(tp):
+    p = inputs.two_asset_min_call(n_grid=16, max_rank=16)
+    rc, prices, _ = gpu_price(tp, [p])
+    exact, _ = integrand.full_grid_price(p)
+    assert abs(prices[0] / exact - 1) < 1e-11
+
+
+def test_two_asset_closed_forms_at_fine_grid(tp):
+    """N=256: the grid sum is within 1e-11 of Stulz (oracle pin); the rank-32 train
+    matches the oracle's train to 1e-6 and the closed form to its TT error (< 1e-6)."""
+    for payoff, f in (("min", closed_forms.stulz_min_call), ("max", closed_forms.stulz_max_call)):
+        p = inputs.two_asset_min_call(n_grid=256, max_rank=32, payoff=payoff)
+        rc, prices, _ = gpu_price(tp, [p])
+        assert abs(prices[0] / oracle_price(p) - 1) < FP64_TOL, payoff
+        ref = f(100, 100, 100, 0.01, 1.0, 0.2, 0.3, 0.5)
+        assert abs(prices[0] / ref - 1) < 1e-6, payoff
+
+
+def test_batch_equals_single_bitwise(tp):
+    ps = [small_problem(3, 20, 5, seed=s) for s in range(3)] + [small_problem(2, 24, 6, payoff="max")]
+    _, batch, _ = gpu_price(tp, ps)
+    for i, p in enumerate(ps):
+        _, one, _ = gpu_price(tp, [p])
+        assert one[0] == batch[i]
+
+
+def test_invalid_problems_get_status_and_nan(tp):
+    good = small_problem(3, 16, 4)
+    bad_pd = good.with_(cov=np.array([[1.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 1.0]]))
+    bad_strip = good.with_(damping=np.array([-0.2, -0.2, -0.2]))
+    bad_sign = good.with_(damping=np.array([0.5, -1.5, -1.5]))
+    too_big = good.with_(max_rank=9)
+    pr = tp.Pricer(max_d=3, max_n=16, max_rank=8, max_batch=5, precision="fp64")
+    rc, prices, diags = pr.evaluate([good, bad_pd, bad_strip, bad_sign, too_big])
+    pr.close()
+    assert [d.status for d in diags] == [diags[0].status, tp.TT_ERR_NOT_PD, tp.TT_ERR_STRIP,
+                                         tp.TT_ERR_STRIP, tp.TT_ERR_CAPACITY]
+    assert diags[0].status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
+    assert math.isfinite(prices[0]) and all(math.isnan(v) for v in prices[1:])
+    assert rc == tp.TT_ERR_CAPACITY or rc < 0
+
+
+def test_empty_batch(tp):
+    pr = tp.Pricer(max_d=2, max_n=16, max_rank=4, max_batch=4, precision="fp64")
+    rc, prices, diags = pr.evaluate([])
+    pr.close()
+    assert rc == tp.TT_OK and prices.size == 0
+
+
+def test_mixed_precision_two_asset(tp):
+    p = inputs.two_asset_min_call(max_rank=8)
+    rc, prices, _ = gpu_price(tp, [p], precision="mixed")
+    assert abs(prices[0] / oracle_price(p) - 1) < MIXED_TOL
+
+
+@pytest.mark.slow
+def test_five_asset_full_size_fp64_and_mixed(tp):
+    """d=5, N=128, rank 32 (the benchmark workload): two seeded instances."""
+    ps = inputs.five_asset_batch(2)
+    refs = [oracle_price(p) for p in ps]
+    _, p64, d64 = gpu_price(tp, ps, precision="fp64")
+    _, pmx, _ = gpu_price(tp, ps, precision="mixed")
+    for i in range(len(ps)):
+        assert abs(p64[i] / refs[i] - 1) < FP64_TOL
+        assert abs(pmx[i] / refs[i] - 1) < MIXED_TOL
+        sig = np.sqrt(np.diag(ps[i].cov))
+        exact = closed_forms.one_factor_price(ps[i].spot, sig, 0.3, 100.0, 0.02, 1.0, "min")
+        assert abs(p64[i] / exact - 1) < 1e-4
