@@ -99,6 +99,12 @@ typedef struct {
   int final_rank_max;    /* largest TT rank after rank reduction                   */
   int terms;             /* trains summed: 1 (min-call) or d (max-call)            */
   long long evaluations; /* integrand evaluations, fiber entries counted once      */
+  long long maxvol_swaps; /* row swaps made by maxvol, all cores and half-sweeps    */
+  long long block_visits; /* maxvol block visits (one block product B = A P^{-1} each) */
+  int fail_step;         /* for TT_ERR_NUMERIC: 1 fiber of rank 0, 2 singular pivot
+                            block in maxvol, 3 singular interpolation solve,
+                            4 non-finite estimate; 5 initial pivots not drawable   */
+  int reserved;
   double imag_part;      /* Im of the discrete sum; 0 up to the TT error           */
   double flops;          /* arithmetic of the elimination, maxvol, interpolation
                             and integrand steps, by formula (see DESIGN notes)     */

@@ -21,7 +21,15 @@ namespace ttp {
 // the persistent kernel: one CTA = one TT-cross job at a time
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __restrict__ jobs,
+struct MinBlocks {
+#ifndef TTP_MIN_BLOCKS_F32
+#define TTP_MIN_BLOCKS_F32 3
+#endif
+  static constexpr int value = sizeof(R) == 4 ? TTP_MIN_BLOCKS_F32 : 1;  // FP32: several CTAs per SM
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel(const JobDesc* __restrict__ jobs,
                                                             const double* __restrict__ params,
                                                             const int* __restrict__ order, int njobs,
                                                             int* counter, JobResult* results,
@@ -29,9 +37,12 @@ __global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __res
                                                             Knobs kn) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double dscr[32];
+  // The context is uniform across the CTA: keeping it in shared memory (written
+  // by thread 0) keeps its ~40 pointers out of every thread's registers.
+  __shared__ Ctx<R> x;
   const int tid = threadIdx.x;
-  Ctx<R> x;
   char* base = scratch + (size_t)blockIdx.x * lay.stride;
+  if (tid == 0) {
   x.dmax = lay.dmax;
   x.nmax = lay.nmax;
   x.rall = lay.rmax;
@@ -44,21 +55,17 @@ __global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __res
   x.rstate = reinterpret_cast<double*>(base + lay.rstate);
   x.lvec = reinterpret_cast<double*>(base + lay.lvec);
   x.rvec = reinterpret_cast<double*>(base + lay.rvec);
-  {
-    R* pr = reinterpret_cast<R*>(base + lay.pair);
-    const size_t plane = (size_t)lay.rmax * lay.rmax;
-    x.pE0 = pr;
-    x.pH = pr + plane;
-    x.pS0 = pr + 2 * plane;
-    x.pOre = pr + 3 * plane;
-    x.pOim = pr + 4 * plane;
-  }
+  x.pair = reinterpret_cast<PairE<R>*>(base + lay.pair);
   x.P = reinterpret_cast<cpx<R>*>(base + lay.P);
   x.sacc = reinterpret_cast<double2*>(base + lay.sacc);
   x.vchain = reinterpret_cast<double2*>(base + lay.chain);
   x.ychain = x.vchain + lay.rmax;
   x.sw = reinterpret_cast<cpx<R>*>(smem + sl.sw);
   x.M = reinterpret_cast<cpx<R>*>(smem + sl.m);
+  x.wvals = reinterpret_cast<cpx<R>*>(smem + sl.wvals);
+  x.stage = reinterpret_cast<PairE<R>*>(smem + sl.stage);
+  x.stage_lo = 0;
+  x.stage_n = 0;
   {
     R* tb = reinterpret_cast<R*>(smem + sl.tab);
     x.tl = tb;
@@ -67,19 +74,23 @@ __global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __res
     x.toi = tb + 3 * lay.nmax;
   }
   x.colmax = reinterpret_cast<R*>(smem + sl.colmax);
+  x.cshift = reinterpret_cast<R*>(smem + sl.cshift);
   x.wrow = reinterpret_cast<int*>(smem + sl.wrow);
   x.wnew = reinterpret_cast<int*>(smem + sl.wnew);
   x.jp = reinterpret_cast<int*>(smem + sl.jp);
   x.selr = reinterpret_cast<int*>(smem + sl.selr);
   x.selc = reinterpret_cast<int*>(smem + sl.selc);
-  x.used = smem + sl.used;
   x.redv = reinterpret_cast<R*>(smem + sl.redv);
   x.redi = reinterpret_cast<int*>(smem + sl.redi);
   x.swcol = reinterpret_cast<cpx<R>*>(smem + sl.swcol);
   x.swrow = reinterpret_cast<cpx<R>*>(smem + sl.swrow);
+  x.mcol = reinterpret_cast<cpx<R>*>(smem + sl.mcol);
+  x.redk = reinterpret_cast<unsigned*>(smem + sl.redk);
   x.lsz = reinterpret_cast<int*>(smem + sl.lsz);
   x.rsz = reinterpret_cast<int*>(smem + sl.rsz);
   x.misc = reinterpret_cast<int*>(smem + sl.misc);
+  }
+  __syncthreads();
 
   for (int guard = 0; guard < njobs + 1; ++guard) {  // at most njobs jobs per CTA
     if (tid == 0) x.misc[MISC_JOB] = atomicAdd(counter, 1);
@@ -89,22 +100,27 @@ __global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __res
     const int jid = order[slot];
     const JobDesc jd = jobs[jid];
     const double* prm = params + jd.param_off;
-    x.d = jd.d;
-    x.n = jd.n;
-    x.rmax = jd.rmax;
-    x.cauchy = jd.cauchy;
-    x.D0 = (R)jd.D0;
-    x.T = jd.T;
-    x.cov = prm;
-    x.flops = 0.0;
-    x.evals = 0;
     if (tid == 0) {
+      x.d = jd.d;
+      x.n = jd.n;
+      x.rmax = jd.rmax;
+      x.cauchy = jd.cauchy;
+      x.D0 = (R)jd.D0;
+      x.T = jd.T;
+      x.cov = prm;
+      x.flops = 0.0;
+      x.evals = 0;
+      x.swaps = 0;
+      x.visits = 0;
+      x.fail_step = 0;
       x.misc[MISC_FAIL] = 0;
       x.misc[MISC_DRAW] = 0;
     }
     __syncthreads();
     double norm_sum = 0.0;
+    TTP_TIC(t_js);
     job_setup(x, jd, prm, dscr, norm_sum);
+    TTP_TOC(t_js, 13);
 
     double2 est = make_double2(0.0, 0.0), prev = make_double2(0.0, 0.0);
     int status = x.misc[MISC_DRAW] ? ST_INVALID : ST_NOT_CONVERGED;
@@ -119,17 +135,22 @@ __global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __res
           maxrank = max(maxrank, rho);
           if (x.misc[MISC_FAIL]) break;
         }
+        TTP_TIC(t_cs);
         if (!x.misc[MISC_FAIL]) est = core_sum(x, d - 1, DIR_LR, dscr);
+        TTP_TOC(t_cs, 12);
       } else {
         for (int k = d - 1; k >= 1; --k) {
           const int rho = core_select(x, kn, k, DIR_RL);
           maxrank = max(maxrank, rho);
           if (x.misc[MISC_FAIL]) break;
         }
+        TTP_TIC(t_cs);
         if (!x.misc[MISC_FAIL]) est = core_sum(x, 0, DIR_RL, dscr);
+        TTP_TOC(t_cs, 12);
       }
       hs = s + 1;
       if (x.misc[MISC_FAIL] || !isfinite(est.x) || !isfinite(est.y)) {
+        if (tid == 0 && x.fail_step == 0) x.fail_step = 4;
         status = ST_NUMERIC;
         break;
       }
@@ -153,10 +174,12 @@ __global__ void __launch_bounds__(kThreads) tt_cross_kernel(const JobDesc* __res
       r.norm_sum = norm_sum;
       r.flops = x.flops;
       r.evaluations = x.evals;
+      r.swaps = x.swaps;
+      r.visits = x.visits;
       r.status = status;
       r.half_sweeps = hs;
       r.max_rank = maxrank;
-      r.maxvol_capped = 0;
+      r.fail_step = status == ST_INVALID ? 5 : x.fail_step;
       results[jid] = r;
     }
     __syncthreads();
@@ -174,6 +197,10 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
   r.imag = 0.0;
   r.flops = 0.0;
   r.evaluations = 0;
+  r.swaps = 0;
+  r.visits = 0;
+  r.fail_step = 0;
+  r.pad = 0;
   r.half_sweeps = 0;
   r.max_rank = 0;
   r.terms = count[i];
@@ -188,6 +215,9 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
     r.imag += sc * q.est_im;
     r.flops += q.flops;
     r.evaluations += q.evaluations;
+    r.swaps += q.swaps;
+    r.visits += q.visits;
+    if (q.fail_step != 0 && r.fail_step == 0) r.fail_step = q.fail_step;
     r.half_sweeps = max(r.half_sweeps, q.half_sweeps);
     r.max_rank = max(r.max_rank, q.max_rank);
     if (q.status < 0 && (worst_err == 0 || q.status < worst_err)) worst_err = q.status;
@@ -275,7 +305,7 @@ Layout make_layout(const tt_options& o, bool f64) {
   L.rstate = take(r * 8 * 8);
   L.lvec = take(r * d * 8);
   L.rvec = take(r * d * 8);
-  L.pair = take(5 * r * r * rs);
+  L.pair = take(8 * r * r * rs);
   L.P = take(r * r * 2 * rs);
   L.sacc = take(r * r * 16);
   L.chain = take(2 * r * 16);
@@ -301,18 +331,22 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   S.sw_elems = sw_elems;
   S.sw = take(sw_elems * cs);
   S.m = take(r * r * cs);
+  S.wvals = take(r * r * cs);
+  S.stage = take(ttp::kStageO * r * 8 * rs);
   S.tab = take(4 * n * rs);
   S.colmax = take(r * rs);
+  S.cshift = take((r + 1) * rs);
   S.wrow = take(r * 4);
   S.wnew = take(r * 4);
   S.jp = take(r * 4);
   S.selr = take(r * 4);
   S.selc = take(r * 4);
-  S.used = take(ttp::kThreads);
   S.redv = take(2 * ttp::kWarps * rs);
   S.redi = take(2 * ttp::kWarps * 4);
+  S.redk = take(2 * ttp::kWarps * 4);
   S.swcol = take(std::max(b * cs, r * 16));
   S.swrow = take(2 * r * cs);
+  S.mcol = take(r * cs);
   S.lsz = take((d + 1) * 4);
   S.rsz = take((d + 1) * 4);
   S.misc = take(16 * 4);
@@ -366,11 +400,17 @@ int grid_for(const tt_options& o, const SmemLayout& S, int* grid_out) {
     e = cudaFuncSetAttribute(ttp::tt_cross_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              S.total);
     if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ttp::tt_cross_kernel<double>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttp::tt_cross_kernel<double>,
                                                         ttp::kThreads, S.total);
   } else {
     e = cudaFuncSetAttribute(ttp::tt_cross_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              S.total);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ttp::tt_cross_kernel<float>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttp::tt_cross_kernel<float>,
                                                         ttp::kThreads, S.total);
@@ -643,6 +683,10 @@ int results_impl(tt_pricer* h, double* prices, tt_diag* diag) {
       diag[i].final_rank_max = r.max_rank;
       diag[i].terms = r.terms;
       diag[i].evaluations = r.evaluations;
+      diag[i].maxvol_swaps = r.swaps;
+      diag[i].block_visits = r.visits;
+      diag[i].fail_step = r.fail_step;
+      diag[i].reserved = 0;
       diag[i].imag_part = r.imag;
       diag[i].flops = r.flops;
     }

@@ -197,12 +197,34 @@ __device__ void core_states(Ctx<R>& x, int k, int dir) {
     const double ore = sl[4] * sr[4] - sl[5] * sr[5];
     const double oim = sl[4] * sr[5] + sl[5] * sr[4];
     const int o = dir == DIR_LR ? a : b, c = dir == DIR_LR ? b : a;
-    const int idx = o * x.rall + c;
-    x.pE0[idx] = (R)(e0 * ls);
-    x.pH[idx] = (R)(h * ls);
-    x.pS0[idx] = (R)s0;
-    x.pOre[idx] = (R)ore;
-    x.pOim[idx] = (R)oim;
+    PairE<R> q;
+    q.e0 = (R)(e0 * ls);
+    q.h = (R)(h * ls);
+    q.s0 = (R)s0;
+    q.ore = (R)ore;
+    q.oim = (R)oim;
+    q.pad0 = q.pad1 = q.pad2 = R(0);
+    x.pair[o * x.rall + c] = q;
+  }
+  if (tid == 0) x.stage_n = 0;
+  __syncthreads();
+}
+
+// Copy the pair entries of outer indices olo..ohi (all nc columns) to shared
+// memory when they fit; eval_point then reads them from there.
+template <typename R>
+__device__ void stage_pairs(Ctx<R>& x, int olo, int ohi, int nc) {
+  const int cnt = ohi - olo + 1;
+  __syncthreads();  // nobody may still read the previous stage
+  if (cnt <= kStageO) {
+    for (int idx = threadIdx.x; idx < cnt * nc; idx += kThreads) {
+      const int so = idx / nc, c = idx % nc;
+      x.stage[so * x.rall + c] = x.pair[(olo + so) * x.rall + c];
+    }
+  }
+  if (threadIdx.x == 0) {
+    x.stage_lo = olo;
+    x.stage_n = cnt <= kStageO ? cnt : 0;
   }
   __syncthreads();
 }
@@ -220,6 +242,29 @@ __device__ void load_axis_table(Ctx<R>& x, int k) {
     x.toi[i] = (R)w.y;
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 only: shift every fiber column by a power of two so that its largest
+// entry has magnitude about one.  Elimination pivots and maxvol's B = A P^{-1}
+// are invariant under column scaling, and the contraction step v S P^{-1}
+// sees the same scale in S and P, so the shift changes no result; it keeps
+// |a|^2 and reciprocals inside the FP32 range for columns through far tails.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void column_shifts(Ctx<R>& x, int no, int nc) {
+  if constexpr (Num<R>::kScaleColumns) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, N = x.n, m = no * N;
+    for (int c = warp; c < nc; c += kWarps) {
+      R mx = R(-3.0e38);
+      for (int r = lane; r < m; r += 32) mx = fmax(mx, eval_logmag(x, r / N, r % N, c));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane == 0) x.cshift[c] = ceilf(mx);
+    }
+    if (threadIdx.x == 0) x.flops += 4.0 * (double)m * nc;
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -299,7 +344,10 @@ __device__ void invert_pivots(Ctx<R>& x, int rho) {
       warp_argmax(v, vi);
       if (lane == 0) {
         x.misc[MISC_PIV] = vi;
-        if (!(v > R(0))) x.misc[MISC_FAIL] = 1;
+        if (!(v > R(0))) {
+          x.misc[MISC_FAIL] = 1;
+          x.fail_step = 2;
+        }
       }
     }
     __syncthreads();
@@ -344,81 +392,106 @@ __device__ __forceinline__ void eval_prow(Ctx<R>& x, int j, int g, int rho) {
 }
 
 // ---------------------------------------------------------------------------
-// one core of a half-sweep: tournament, maxvol, interpolation solve
+// GEPP tournament over row blocks: initial rows W and kept columns Jp.
+// The winners' original rows are cached in wvals (column-major, ld rall), so a
+// merge evaluates only its block and the block rows that win.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
-  const int tid = threadIdx.x;
-  const int N = x.n;
-  core_states(x, k, dir);
-  load_axis_table(x, k);
-  const int no = dir == DIR_LR ? x.lsz[k] : x.rsz[k + 1];
-  const int nc = dir == DIR_LR ? x.rsz[k + 1] : x.lsz[k];
-  const int m = no * N;
-  const int b = kn.block_rows;
+__device__ int tournament(Ctx<R>& x, int m, int nc, int b, R thr2) {
+  const int tid = threadIdx.x, N = x.n;
   const int nb = (m + b - 1) / b;
   const int ldq = x.rall + b;
-  const R thr2 = (R)(kn.theta * kn.theta);
-  if (tid == 0) x.evals += (long long)m * nc;
-
-  // ---- GEPP tournament over row blocks ----
   int rho = 0;
   for (int beta = 0; beta < nb; ++beta) {
     const int rs = beta * b;
     const int bs = min(b, m - rs);
     const int q = rho + bs;
-    for (int idx = tid; idx < q * nc; idx += kThreads) {
-      const int r = idx % q, c = idx / q;
-      const int g = r < rho ? x.wrow[r] : rs + r - rho;
-      x.sw[c * ldq + r] = eval_point(x, g / N, g % N, c);
+    TTP_TIC(t_ev);
+    stage_pairs(x, rs / N, (rs + bs - 1) / N, nc);
+    for (int idx = tid; idx < rho * nc; idx += kThreads) {
+      const int t = idx % rho, c = idx / rho;
+      x.sw[c * ldq + t] = x.wvals[c * x.rall + t];
     }
-    if (tid == 0) x.flops += 24.0 * q * nc;
+    for (int idx = tid; idx < bs * nc; idx += kThreads) {
+      const int r = idx % bs, c = idx / bs;
+      const int g = rs + r;
+      x.sw[c * ldq + rho + r] = eval_point(x, g / N, g % N, c);
+    }
+    if (tid == 0) x.flops += 24.0 * bs * nc;
     __syncthreads();
+    TTP_TOC(t_ev, 2);
+    TTP_TIC(t_ge);
     const int nsel = gepp_select(x, q, nc, ldq, thr2);
+    TTP_TOC(t_ge, 3);
+    TTP_TIC(t_ga);
+    // new winners' original rows, gathered into sw (free now), then copied
+    for (int idx = tid; idx < nsel * nc; idx += kThreads) {
+      const int t = idx % nsel, c = idx / nsel;
+      const int cr = x.selr[t];
+      cpx<R> v;
+      if (cr < rho) {
+        v = x.wvals[c * x.rall + cr];
+      } else {
+        const int g = rs + cr - rho;
+        v = eval_point(x, g / N, g % N, c);
+      }
+      x.sw[c * x.rall + t] = v;
+    }
     for (int t = tid; t < nsel; t += kThreads) {
       const int cr = x.selr[t];
       x.wnew[t] = cr < rho ? x.wrow[cr] : rs + cr - rho;
     }
     __syncthreads();
+    for (int idx = tid; idx < nsel * nc; idx += kThreads) {
+      const int t = idx % nsel, c = idx / nsel;
+      x.wvals[c * x.rall + t] = x.sw[c * x.rall + t];
+    }
     for (int t = tid; t < nsel; t += kThreads) {
       x.wrow[t] = x.wnew[t];
       x.jp[t] = x.selc[t];
     }
     rho = nsel;
     __syncthreads();
+    TTP_TOC(t_ga, 4);
   }
-  if (rho == 0) {
-    if (tid == 0) x.misc[MISC_FAIL] = 1;
-    __syncthreads();
-    return 0;
-  }
+  return rho;
+}
 
-  // ---- pivot rows and cyclic block maxvol on the kept columns ----
-  for (int idx = tid; idx < rho * rho; idx += kThreads) {
-    const int j = idx / rho, t = idx % rho;
-    const int g = x.wrow[j];
-    x.P[j * x.rall + t] = eval_point(x, g / N, g % N, x.jp[t]);
-  }
+// ---------------------------------------------------------------------------
+// cyclic block maxvol on the kept columns (rows W start from the tournament)
+// P holds A[W, Jp]; M = P^{-1} is kept current by rank-one (Sherman-Morrison)
+// updates at each swap and recomputed after kRefreshSwaps of them.
+// The first cycle also accumulates the row sums S[o, t] = sum_i A[(o,i), Jp[t]].
+// ---------------------------------------------------------------------------
+constexpr int kRefreshSwaps = 16;
+
+template <typename R>
+__device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
+  const int tid = threadIdx.x, N = x.n;
+  const int nb = (m + b - 1) / b;
   for (int idx = tid; idx < no * rho; idx += kThreads) {
     const int o = idx / rho, t = idx % rho;
     x.sacc[o * x.rall + t] = make_double2(0.0, 0.0);
   }
-  __syncthreads();
-  const R thr = (R)((1.0 + kn.tau) * (1.0 + kn.tau));
-  int quiet = 0, visits = 0, beta = 0;
-  bool mvalid = false;
+  int quiet = 0, visits = 0, beta = 0, since_inv = kRefreshSwaps;
   int buf = 0;
+  long long nswaps = 0;
   const int nct = (rho + 3) / 4;
-  const int rtiles = kThreads / nct;  // row tiles per round
+  const int rtiles = kThreads / nct;  // row tiles per round: thread (rt, ct) owns rows rt + a*rtiles
   const int rpr = 4 * rtiles;
   while (quiet < nb && visits < 4 * nb) {
-    if (!mvalid) {
+    if (since_inv >= kRefreshSwaps) {
+      TTP_TIC(t_inv);
       invert_pivots(x, rho);
-      mvalid = true;
+      since_inv = 0;
+      TTP_TOC(t_inv, 5);
     }
+    TTP_TIC(t_rev);
     const int rs = beta * b;
     const int bs = min(b, m - rs);
     cpx<R>* A = x.sw;  // bs x rho, column-major, leading dimension b
+    // stage_pairs needs the kept columns' entries: stage all columns up to the largest kept one
+    stage_pairs(x, rs / N, (rs + bs - 1) / N, x.jp[rho - 1] + 1);
     for (int idx = tid; idx < bs * rho; idx += kThreads) {
       const int r = idx % bs, t = idx / bs;
       const int g = rs + r;
@@ -426,7 +499,9 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
     }
     if (tid == 0) x.flops += 24.0 * bs * rho + 8.0 * (double)bs * rho * rho;
     __syncthreads();
-    if (visits < nb) {  // first pass: accumulate the fiber's row sums over i per outer index
+    TTP_TOC(t_rev, 6);
+    TTP_TIC(t_gemm);
+    if (visits < nb) {  // first cycle: row sums over i per outer index
       const int olo = rs / N, ohi = (rs + bs - 1) / N;
       const int nol = ohi - olo + 1;
       for (int idx = tid; idx < nol * rho; idx += kThreads) {
@@ -444,13 +519,13 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
         acc.y += (double)si;
       }
     }
-    // B = A M in row strips; every strip is read completely before it is overwritten
+    // B = A M in row strips; each strip is read completely before it is overwritten
     R bv = R(-1);
     int bi = INT_MAX;
     for (int r0 = 0; r0 < bs; r0 += rpr) {
       const int rt = tid % rtiles, ct = tid / rtiles;
-      const int row0 = r0 + 4 * rt, col0 = 4 * ct;
-      const bool act = ct < nct && row0 < bs;
+      const int col0 = 4 * ct;
+      const bool act = ct < nct && r0 + rt < bs;
       cpx<R> acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -460,7 +535,10 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
         for (int t = 0; t < rho; ++t) {
           cpx<R> av[4], mv[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = (row0 + a < bs) ? A[t * b + row0 + a] : cpx<R>{R(0), R(0)};
+          for (int a = 0; a < 4; ++a) {
+            const int r = r0 + rt + a * rtiles;
+            av[a] = r < bs ? A[t * b + r] : cpx<R>{R(0), R(0)};
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c)
             mv[c] = (col0 + c < rho) ? x.M[t * x.rall + col0 + c] : cpx<R>{R(0), R(0)};
@@ -476,7 +554,7 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const int r = row0 + a, cc = col0 + c;
+            const int r = r0 + rt + a * rtiles, cc = col0 + c;
             if (r < bs && cc < rho) {
               A[cc * b + r] = acc[a][c];
               am_merge(bv, bi, cabs2(acc[a][c]), r * rho + cc);
@@ -486,12 +564,17 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
     }
     buf ^= 1;
     block_argmax(bv, bi, x.redv, x.redi, buf);
+    TTP_TOC(t_gemm, 8);
+    TTP_TIC(t_sw);
     bool swapped = false;
     for (int it = 0; it < rho; ++it) {
       if (!(bv > thr)) break;
       const int i = bi / rho, j = bi % rho;
       for (int r = tid; r < bs; r += kThreads) x.swcol[r] = A[j * b + r];
-      for (int t = tid; t < rho; t += kThreads) x.swrow[t] = A[t * b + i];
+      for (int t = tid; t < rho; t += kThreads) {
+        x.swrow[t] = A[t * b + i];
+        x.mcol[t] = x.M[t * x.rall + j];
+      }
       if (tid == 0) x.wrow[j] = rs + i;
       __syncthreads();
       eval_prow(x, j, rs + i, rho);
@@ -507,19 +590,37 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
         A[t * b + r] = bb;
         am_merge(bv, bi, cabs2(bb), r * rho + t);
       }
-      if (tid == 0) x.flops += 8.0 * bs * rho + 24.0 * rho;
+      for (int idx = tid; idx < rho * rho; idx += kThreads) {
+        const int r = idx / rho, t = idx % rho;
+        cpx<R> rv = x.swrow[t];
+        if (t == j) rv.re -= R(1);
+        cfms(x.M[r * x.rall + t], x.mcol[r], cmul(rv, ipiv));
+      }
+      if (tid == 0) x.flops += 8.0 * (bs + rho) * rho + 24.0 * rho;
       buf ^= 1;
       block_argmax(bv, bi, x.redv, x.redi, buf);
       swapped = true;
-      mvalid = false;
+      ++since_inv;
+      ++nswaps;
     }
     quiet = swapped ? 0 : quiet + 1;
     ++visits;
     beta = (beta + 1) % nb;
     __syncthreads();
+    TTP_TOC(t_sw, 9);
   }
+  if (tid == 0) {
+    x.swaps += nswaps;
+    x.visits += visits;
+  }
+}
 
-  // ---- contraction step: v <- (v S) P^{-1}, FP64 (Gaussian elimination on P^T) ----
+// ---------------------------------------------------------------------------
+// contraction step: v <- (v S) P^{-1}, FP64 (Gaussian elimination on P^T)
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void chain_solve(Ctx<R>& x, int no, int rho) {
+  const int tid = threadIdx.x;
   for (int t = tid; t < rho; t += kThreads) {
     double2 y = make_double2(0.0, 0.0);
     for (int o = 0; o < no; ++o) {
@@ -555,7 +656,10 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
       warp_argmax(v, vi);
       if (lane == 0) {
         x.misc[MISC_PIV] = vi;
-        if (!(v > 0.0)) x.misc[MISC_FAIL] = 1;
+        if (!(v > 0.0)) {
+          x.misc[MISC_FAIL] = 1;
+          x.fail_step = 3;
+        }
       }
     }
     __syncthreads();
@@ -611,8 +715,47 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
   }
   if (tid == 0) x.flops += 8.0 * (double)no * rho + 8.0 * (double)rho * rho * rho / 3.0;
   __syncthreads();
+}
 
-  // ---- new index set ----
+// ---------------------------------------------------------------------------
+// one core of a half-sweep: tournament, maxvol, interpolation solve, new index set
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
+  const int tid = threadIdx.x;
+  const int N = x.n;
+  TTP_TIC(t_st);
+  core_states(x, k, dir);
+  load_axis_table(x, k);
+  TTP_TOC(t_st, 0);
+  const int no = dir == DIR_LR ? x.lsz[k] : x.rsz[k + 1];
+  const int nc = dir == DIR_LR ? x.rsz[k + 1] : x.lsz[k];
+  const int m = no * N;
+  const int b = kn.block_rows;
+  if (tid == 0) x.evals += (long long)m * nc;
+  TTP_TIC(t_cs);
+  column_shifts(x, no, nc);
+  TTP_TOC(t_cs, 1);
+  const int rho = tournament(x, m, nc, b, (R)(kn.theta * kn.theta));
+  if (rho == 0) {
+    if (tid == 0) {
+      x.misc[MISC_FAIL] = 1;
+      x.fail_step = 1;
+    }
+    __syncthreads();
+    return 0;
+  }
+  // P = A[W, Jp] from the cached winner rows
+  for (int idx = tid; idx < rho * rho; idx += kThreads) {
+    const int j = idx / rho, t = idx % rho;
+    x.P[j * x.rall + t] = x.wvals[x.jp[t] * x.rall + j];
+  }
+  __syncthreads();
+  maxvol_refine(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));
+  TTP_TIC(t_ch);
+  chain_solve(x, no, rho);
+  TTP_TOC(t_ch, 10);
+  // new index set
   if (dir == DIR_LR) {
     const int w = k + 1;
     for (int idx = tid; idx < rho * w; idx += kThreads) {
@@ -634,6 +777,7 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
   return rho;
 }
 
+
 // end core of a half-sweep: est = sum_o v[o] * sum_i A[(o,i)]
 template <typename R>
 __device__ double2 core_sum(Ctx<R>& x, int k, int dir, double* dscr) {
@@ -641,6 +785,7 @@ __device__ double2 core_sum(Ctx<R>& x, int k, int dir, double* dscr) {
   core_states(x, k, dir);
   load_axis_table(x, k);
   const int no = dir == DIR_LR ? x.lsz[k] : x.rsz[k + 1];
+  column_shifts(x, no, 1);
   double2 est = make_double2(0.0, 0.0);
   for (int o = 0; o < no; ++o) {
     double2 s = make_double2(0.0, 0.0);
@@ -657,6 +802,11 @@ __device__ double2 core_sum(Ctx<R>& x, int k, int dir, double* dscr) {
   if (tid == 0) {
     x.evals += (long long)no * N;
     x.flops += 24.0 * (double)no * N;
+  }
+  if constexpr (Num<R>::kScaleColumns) {
+    const double sc = exp2((double)x.cshift[0]);
+    est.x *= sc;
+    est.y *= sc;
   }
   return est;
 }

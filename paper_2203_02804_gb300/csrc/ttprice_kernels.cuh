@@ -22,6 +22,25 @@
 
 namespace ttp {
 
+// Optional per-phase cycle counters (profiling builds only: -DTTP_PHASE_TIMERS).
+// Thread 0 of each CTA adds the clock64() span of each phase; the totals show
+// where a CTA's time goes, waits at barriers included.
+#ifdef TTP_PHASE_TIMERS
+__device__ unsigned long long g_phase_cycles[16];
+#define TTP_TIC(v) const long long v = clock64()
+#define TTP_TOC(v, slot)                                                            \
+  do {                                                                              \
+    if (threadIdx.x == 0) atomicAdd(&g_phase_cycles[slot], (unsigned long long)(clock64() - (v))); \
+  } while (0)
+#else
+#define TTP_TIC(v) \
+  do {             \
+  } while (0)
+#define TTP_TOC(v, slot) \
+  do {                   \
+  } while (0)
+#endif
+
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
@@ -54,21 +73,29 @@ template <typename R>
 __device__ __forceinline__ R cabs2(cpx<R> a) {
   return a.re * a.re + a.im * a.im;
 }
+// 1/a by Smith's method (Smith 1962): no squares of the operands, so it stays
+// finite for any nonzero a in range.
 template <typename R>
 __device__ __forceinline__ cpx<R> crecip(cpx<R> a) {
-  R s = R(1) / cabs2(a);
-  return {a.re * s, -a.im * s};
+  if (fabs(a.re) >= fabs(a.im)) {
+    const R r = a.im / a.re, den = a.re + a.im * r;
+    return {R(1) / den, -r / den};
+  }
+  const R r = a.re / a.im, den = a.re * r + a.im;
+  return {r / den, R(-1) / den};
 }
 
 // exp of the log-magnitude: FP32 tables hold E in log2 units, FP64 in natural units.
 template <typename R> struct Num;
 template <> struct Num<float> {
   static constexpr double kLogScale = 1.4426950408889634;  // log2(e)
+  static constexpr bool kScaleColumns = true;  // FP32 range needs per-column power-of-two scaling
   __device__ static __forceinline__ float ex(float e) { return exp2f(e); }
   __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
 };
 template <> struct Num<double> {
   static constexpr double kLogScale = 1.0;
+  static constexpr bool kScaleColumns = false;
   __device__ static __forceinline__ double ex(double e) { return exp(e); }
   __device__ static __forceinline__ double div(double a, double b) { return a / b; }
 };
@@ -91,14 +118,14 @@ struct JobResult {
   double est_re, est_im;  // TT sum of the normalised integrand
   double norm_sum;        // sum over axes of the per-axis log normalisation
   double flops;
-  long long evaluations;
-  int status, half_sweeps, max_rank, maxvol_capped;
+  long long evaluations, swaps, visits;
+  int status, half_sweeps, max_rank, fail_step;
 };
 
 struct InstanceResult {
   double price, imag, flops;
-  long long evaluations;
-  int status, half_sweeps, max_rank, terms;
+  long long evaluations, swaps, visits;
+  int status, half_sweeps, max_rank, terms, fail_step, pad;
 };
 
 struct Knobs {
@@ -109,7 +136,7 @@ struct Knobs {
   int block_rows;
 };
 
-// per-CTA global scratch, byte offsets
+// per-CTA global scratch, byte offsets (pair: PairE<R> entries)
 struct Layout {
   size_t u, lam, om, lset, rset, lstate, rstate, lvec, rvec, pair, P, sacc, chain, stride;
   int dmax, nmax, rmax;
@@ -117,8 +144,8 @@ struct Layout {
 
 // shared-memory carve, byte offsets (sizes depend on R)
 struct SmemLayout {
-  int sw, m, tab, colmax, wrow, wnew, jp, selr, selc, used, redv, redi, swcol, swrow, lsz, rsz,
-      misc, total;
+  int sw, m, wvals, stage, tab, colmax, cshift, wrow, wnew, jp, selr, selc, redv, redi, redk, swcol,
+      swrow, mcol, lsz, rsz, misc, total;
   int sw_elems;
 };
 
@@ -132,13 +159,24 @@ __device__ __forceinline__ void am_merge(R& v, int& i, R v2, int i2) {
     i = i2;
   }
 }
+// Values are magnitudes (>= 0) or -1 for "no candidate"; NaN never wins.
 template <typename R>
 __device__ __forceinline__ void warp_argmax(R& v, int& i) {
+  if constexpr (sizeof(R) == 4) {
+    // non-negative floats order like their bit patterns: two warp reductions
+    const unsigned key = (v >= R(0)) ? __float_as_uint(v) + 1u : 0u;
+    const unsigned mk = __reduce_max_sync(0xffffffffu, key);
+    const unsigned mi = __reduce_min_sync(0xffffffffu, key == mk ? (unsigned)i : 0xffffffffu);
+    v = mk == 0u ? R(-1) : __uint_as_float(mk - 1u);
+    i = (int)mi;
+  } else {
+    if (!(v >= R(0))) v = R(-1);  // NaN would make lanes disagree
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    R v2 = __shfl_xor_sync(0xffffffffu, v, off);
-    int i2 = __shfl_xor_sync(0xffffffffu, i, off);
-    am_merge(v, i, v2, i2);
+    for (int off = 16; off > 0; off >>= 1) {
+      R v2 = __shfl_xor_sync(0xffffffffu, v, off);
+      int i2 = __shfl_xor_sync(0xffffffffu, i, off);
+      am_merge(v, i, v2, i2);
+    }
   }
 }
 // Writes the warp partial into buffer `buf`, syncs, and returns the block result
@@ -186,6 +224,19 @@ __device__ __forceinline__ long long ipow_cap(long long n, int e, long long cap)
 // ---------------------------------------------------------------------------
 // per-CTA context
 // ---------------------------------------------------------------------------
+// Pair entry of core k for (outer index o, column c): everything about the
+// integrand at fiber point (o, i, c) that does not depend on the grid index i.
+template <typename R>
+struct alignas(8 * sizeof(R)) PairE {
+  R e0;   // log-magnitude part (scaled units)
+  R h;    // coefficient of u_i in the log-magnitude
+  R s0;   // sum of the other coordinates (for 1/(D0 + i sum u))
+  R ore, oim;  // unit phase of the other coordinates
+  R pad0, pad1, pad2;
+};
+
+constexpr int kStageO = 4;  // outer indices whose pair entries a block stages in shared memory
+
 template <typename R>
 struct Ctx {
   // job
@@ -204,11 +255,7 @@ struct Ctx {
   double* rstate;
   double* lvec;       // [rmax_all][dmax]
   double* rvec;
-  R* pE0;
-  R* pH;
-  R* pS0;
-  R* pOre;
-  R* pOim;  // [rmax_all][rmax_all]
+  PairE<R>* pair;     // [rmax_all][rmax_all]
   cpx<R>* P;          // [rmax_all][rmax_all] pivot rows A[W, Jp]
   double2* sacc;      // [rmax_all][rmax_all]
   double2* vchain;    // [rmax_all]
@@ -217,27 +264,33 @@ struct Ctx {
   // shared
   cpx<R>* sw;
   cpx<R>* M;
+  cpx<R>* wvals;      // [rmax_all cols][rmax_all rows] original values of the current winners
+  PairE<R>* stage;    // [kStageO][rmax_all]
+  int stage_lo, stage_n;
   R* tl;  // [nmax] lam' of the active axis (scaled)
   R* tu;  // [nmax] u
   R* tor;
   R* toi;
   R* colmax;
+  R* cshift;  // per-column exponent shift (log2 units, integer valued), FP32 only
   int* wrow;
   int* wnew;
   int* jp;
   int* selr;
   int* selc;
-  unsigned char* used;
   R* redv;
   int* redi;
+  unsigned* redk;
   cpx<R>* swcol;
   cpx<R>* swrow;
+  cpx<R>* mcol;
   int* lsz;
   int* rsz;
   int* misc;
   // bookkeeping (thread 0 only)
   double flops;
-  long long evals;
+  long long evals, swaps, visits;
+  int fail_step;
 };
 
 // Index sets: left set at bond k holds multi-indices over axes 0..k-1,
@@ -251,17 +304,33 @@ __device__ __forceinline__ uint16_t* rset_at(const Ctx<R>& x, int k, int b) {
   return x.rset + ((size_t)k * x.rall + b) * x.dmax;
 }
 
+template <typename R>
+__device__ __forceinline__ const PairE<R>& pair_at(const Ctx<R>& x, int o, int col) {
+  const int so = o - x.stage_lo;
+  if (so >= 0 && so < x.stage_n) return x.stage[so * x.rall + col];
+  return x.pair[o * x.rall + col];
+}
+
+// log-magnitude (scaled units) of the integrand at one fiber point, before shifts
+template <typename R>
+__device__ __forceinline__ R eval_logmag(const Ctx<R>& x, int o, int i, int col) {
+  const PairE<R>& q = pair_at(x, o, col);
+  return q.e0 + x.tl[i] + q.h * x.tu[i];
+}
+
 // ---------------------------------------------------------------------------
 // integrand at one fiber point
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ cpx<R> eval_point(const Ctx<R>& x, int o, int i, int col) {
-  const int p = o * x.rall + col;
-  const R e = x.pE0[p] + x.tl[i] + x.pH[p] * x.tu[i];
-  cpx<R> w = cmul(cpx<R>{x.pOre[p], x.pOim[p]}, cpx<R>{x.tor[i], x.toi[i]});
+  const PairE<R> q = pair_at(x, o, col);
+  const R ui = x.tu[i];
+  R e = q.e0 + x.tl[i] + q.h * ui;
+  if constexpr (Num<R>::kScaleColumns) e -= x.cshift[col];
+  cpx<R> w = cmul(cpx<R>{q.ore, q.oim}, cpx<R>{x.tor[i], x.toi[i]});
   R f = Num<R>::ex(e);
   if (x.cauchy) {
-    const R s = x.pS0[p] + x.tu[i];
+    const R s = q.s0 + ui;
     const R den = fma(s, s, x.D0 * x.D0);
     f = Num<R>::div(f, den);
     w = cmul(w, cpx<R>{x.D0, -s});

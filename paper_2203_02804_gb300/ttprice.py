@@ -56,7 +56,9 @@ class tt_problem(ctypes.Structure):
 class tt_diag(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("half_sweeps", ctypes.c_int),
                 ("final_rank_max", ctypes.c_int), ("terms", ctypes.c_int),
-                ("evaluations", ctypes.c_longlong), ("imag_part", ctypes.c_double),
+                ("evaluations", ctypes.c_longlong), ("maxvol_swaps", ctypes.c_longlong),
+                ("block_visits", ctypes.c_longlong), ("fail_step", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("imag_part", ctypes.c_double),
                 ("flops", ctypes.c_double)]
 
 
@@ -109,6 +111,10 @@ class Diag:
     final_rank_max: int
     terms: int
     evaluations: int
+    maxvol_swaps: int
+    block_visits: int
+    fail_step: int
+    reserved: int
     imag_part: float
     flops: float
 

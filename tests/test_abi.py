@@ -64,7 +64,8 @@ def test_struct_layouts_match_c():
              offsetof(tt_options, workspace_bytes));
       printf("%zu %zu %zu %zu %zu\n", sizeof(tt_problem), offsetof(tt_problem, rate),
              offsetof(tt_problem, damping), offsetof(tt_problem, trunc_L), offsetof(tt_problem, seed));
-      printf("%zu %zu %zu\n", sizeof(tt_diag), offsetof(tt_diag, evaluations), offsetof(tt_diag, flops));
+      printf("%zu %zu %zu %zu\n", sizeof(tt_diag), offsetof(tt_diag, evaluations), offsetof(tt_diag, fail_step),
+             offsetof(tt_diag, flops));
       return 0;
     }
     """
@@ -80,7 +81,8 @@ def test_struct_layouts_match_c():
          T.tt_options.cuda_stream.offset, T.tt_options.workspace_bytes.offset],
         [ctypes.sizeof(T.tt_problem), T.tt_problem.rate.offset, T.tt_problem.damping.offset,
          T.tt_problem.trunc_L.offset, T.tt_problem.seed.offset],
-        [ctypes.sizeof(T.tt_diag), T.tt_diag.evaluations.offset, T.tt_diag.flops.offset],
+        [ctypes.sizeof(T.tt_diag), T.tt_diag.evaluations.offset, T.tt_diag.fail_step.offset,
+         T.tt_diag.flops.offset],
     ]
     for line, w in zip(out, want):
         assert [int(v) for v in line.split()] == w

@@ -152,9 +152,20 @@ def test_empty_batch(tp):
 
 
 def test_mixed_precision_two_asset(tp):
-    p = inputs.two_asset_min_call(max_rank=8)
-    rc, prices, _ = gpu_price(tp, [p], precision="mixed")
+    """At rank 32 the train is converged (TT error ~1e-9), so the FP32 path, whose
+    pivot decisions may part from FP64 at near-ties, must land within 1e-4."""
+    p = inputs.two_asset_min_call(max_rank=32)
+    rc, prices, diags = gpu_price(tp, [p], precision="mixed")
+    assert diags[0].status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
     assert abs(prices[0] / oracle_price(p) - 1) < MIXED_TOL
+
+
+def test_mixed_precision_small_batch(tp):
+    ps = [small_problem(3, 37, 12, seed=s) for s in range(4)] + [small_problem(3, 24, 12, payoff="max")]
+    _, prices, diags = gpu_price(tp, ps, precision="mixed")
+    for p, v, dg in zip(ps, prices, diags):
+        assert dg.status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
+        assert abs(v / oracle_price(p) - 1) < MIXED_TOL
 
 
 @pytest.mark.slow
