@@ -829,3 +829,4 @@ const char* tt_status_string(int status) {
 }
 
 }  // extern "C"
+
