@@ -143,6 +143,36 @@ int tt_price_results(tt_pricer* h, double* prices, tt_diag* diag);
  * tt_price_results copied device-to-host (for end-to-end accounting). */
 int tt_price_transfer_bytes(const tt_pricer* h, size_t* h2d, size_t* d2h);
 
+/* Allocation-free pricing, for callers that may not allocate memory in the
+ * call: code running where an allocation can fail or stall (a latency-bound
+ * quote loop, a plugin inside a host application that owns all device memory,
+ * a process whose memory budget is fixed up front).  The paper has no
+ * counterpart; it is a deployment aid.
+ *
+ * Prices count <= TT_STATIC_MAX_BATCH problems, each with d <= TT_STATIC_MAX_D,
+ * n_grid <= TT_STATIC_MAX_N and max_rank <= TT_STATIC_MAX_RANK, with the default
+ * tolerances of tt_options, on the current CUDA device and the given stream
+ * (NULL = legacy default stream).  Same results as tt_price_evaluate with those
+ * options.  Blocking, like tt_price_evaluate.
+ *  - Memory: no cudaMalloc/cudaFree/host allocation.  Device scratch is one
+ *    file-scope array of TT_STATIC_SCRATCH_BYTES that every GPU loading this
+ *    library holds until the process exits; host staging is file-scope arrays.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and sets kernel attributes; make that first call
+ *    before any stream capture on that device.
+ *  - Every call reuses the same arrays and overwrites the previous call's
+ *    contents.  Calls that overlap (other threads, other streams) race; callers
+ *    must serialise them.
+ *  - Returns TT_ERR_CAPACITY if count exceeds TT_STATIC_MAX_BATCH; a problem
+ *    beyond the size limits gets TT_ERR_CAPACITY in its tt_diag and a NaN price. */
+#define TT_STATIC_MAX_BATCH 64
+#define TT_STATIC_MAX_D 8
+#define TT_STATIC_MAX_N 256
+#define TT_STATIC_MAX_RANK 32
+#define TT_STATIC_SCRATCH_BYTES (16u << 20)
+int tt_price_evaluate_static(const tt_problem* probs, int count, int precision, void* cuda_stream,
+                             double* prices, tt_diag* diag);
+
 /* Release everything the handle owns.  NULL-safe. */
 void tt_price_destroy(tt_pricer* h);
 

@@ -830,3 +830,298 @@ const char* tt_status_string(int status) {
 
 }  // extern "C"
 
+// ===========================================================================
+// Allocation-free entry point (tt_price_evaluate_static): for callers that may
+// not allocate device or host memory.  Its scratch is one file-scope device
+// array; its host staging is file-scope host arrays.  It shares the kernels and
+// the launch/result code above, and has its own fixed-size preparation.
+// ===========================================================================
+namespace {
+
+constexpr int kStaticJobs = TT_STATIC_MAX_BATCH * TT_STATIC_MAX_D;
+constexpr size_t kStaticParams = (size_t)kStaticJobs * (TT_STATIC_MAX_D * TT_STATIC_MAX_D + 3 * TT_STATIC_MAX_D);
+constexpr size_t kStaticStageBytes =
+    (sizeof(JobDesc) * kStaticJobs + 255) / 256 * 256 + (sizeof(double) * kStaticParams + 255) / 256 * 256 +
+    (sizeof(int) * kStaticJobs + 255) / 256 * 256 + 3 * ((sizeof(int) * TT_STATIC_MAX_BATCH + 255) / 256 * 256);
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[TT_STATIC_SCRATCH_BYTES];
+
+alignas(256) static unsigned char g_static_stage[kStaticStageBytes];
+alignas(256) static unsigned char g_static_pack[kStaticStageBytes];
+alignas(256) static InstanceResult g_static_ires[TT_STATIC_MAX_BATCH];
+
+struct StaticDevice {
+  bool ready;
+  char* scratch;  // device address of g_static_scratch on this device
+  int grid[2];    // CTAs per precision that fit in the array and on the GPU
+};
+static StaticDevice g_static_dev[kStaticMaxDevices];
+
+tt_options static_options(int precision, int device, void* stream) {
+  tt_options o;
+  std::memset(&o, 0, sizeof(o));
+  o.max_d = TT_STATIC_MAX_D;
+  o.max_n = TT_STATIC_MAX_N;
+  o.max_rank = TT_STATIC_MAX_RANK;
+  o.max_batch = TT_STATIC_MAX_BATCH;
+  o.precision = precision == TT_MIXED ? TT_MIXED : TT_FP64;
+  o.device = device;
+  o.cuda_stream = stream;
+  return o;
+}
+
+// Cholesky test without heap memory (d <= TT_STATIC_MAX_D)
+bool cholesky_ok_small(const double* c, int d) {
+  double l[TT_STATIC_MAX_D * TT_STATIC_MAX_D] = {0.0};
+  double scale = 0.0;
+  for (int i = 0; i < d * d; ++i) scale = std::max(scale, std::fabs(c[i]));
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(c[i * d + j] - c[j * d + i]) > 1e-12 * scale) return false;
+  for (int j = 0; j < d; ++j) {
+    double s = c[j * d + j];
+    for (int k = 0; k < j; ++k) s -= l[j * d + k] * l[j * d + k];
+    if (!(s > 0.0)) return false;
+    const double ljj = std::sqrt(s);
+    l[j * d + j] = ljj;
+    for (int i = j + 1; i < d; ++i) {
+      double t = c[i * d + j];
+      for (int k = 0; k < j; ++k) t -= l[i * d + k] * l[j * d + k];
+      l[i * d + j] = t / ljj;
+    }
+  }
+  return true;
+}
+
+// Validation and per-train derivation into the handle's host stage, with no
+// heap use (fixed arrays, in-place sort); same rules and formulas as the
+// handle-based preparation.
+int prepare_static(tt_pricer* h, const tt_problem* probs, int count) {
+  const tt_options& o = h->R.o;
+  char* st = h->h_stage;
+  JobDesc* jobs = reinterpret_cast<JobDesc*>(st + h->dl.o_jobs);
+  double* params = reinterpret_cast<double*>(st + h->dl.o_params);
+  int* order = reinterpret_cast<int*>(st + h->dl.o_order);
+  int* first = reinterpret_cast<int*>(st + h->dl.o_first);
+  int* cnt = reinterpret_cast<int*>(st + h->dl.o_count);
+  int* hstat = reinterpret_cast<int*>(st + h->dl.o_hstatus);
+  int nj = 0;
+  size_t poff = 0;
+  for (int i = 0; i < count; ++i) {
+    const tt_problem& p = probs[i];
+    first[i] = nj;
+    cnt[i] = 0;
+    hstat[i] = TT_OK;
+    const int d = p.d;
+    int stv = TT_OK;
+    if (d < 1 || d > o.max_d || p.n_grid < 2 || p.n_grid > o.max_n || p.max_rank < 1 ||
+        p.max_rank > o.max_rank || !p.spot || !p.cov || !p.damping ||
+        (p.payoff != TT_MIN_CALL && p.payoff != TT_MAX_CALL))
+      stv = (d > o.max_d || p.n_grid > o.max_n || p.max_rank > o.max_rank) ? TT_ERR_CAPACITY
+                                                                             : TT_ERR_INVALID;
+    else if (!(p.trunc_L > 0) || !std::isfinite(p.trunc_L) || !(p.maturity > 0) ||
+             !std::isfinite(p.maturity) || !(p.strike > 0) || !std::isfinite(p.strike) ||
+             !std::isfinite(p.rate) || !finite_all(p.spot, d) || !finite_all(p.cov, d * d) ||
+             !finite_all(p.damping, d))
+      stv = TT_ERR_INVALID;
+    else {
+      for (int j = 0; j < d; ++j)
+        if (!(p.spot[j] > 0)) stv = TT_ERR_INVALID;
+      if (stv == TT_OK && !cholesky_ok_small(p.cov, d)) stv = TT_ERR_NOT_PD;
+      if (stv == TT_OK) {
+        if (p.payoff == TT_MIN_CALL) {
+          double sd = 0.0;
+          for (int j = 0; j < d; ++j) {
+            if (!(-p.damping[j] > 0)) stv = TT_ERR_STRIP;
+            sd += -p.damping[j];
+          }
+          if (!(sd > 1.0)) stv = TT_ERR_STRIP;
+        } else {
+          for (int j = 0; j < d; ++j)
+            if (!(std::fabs(p.damping[j]) > 0)) stv = TT_ERR_STRIP;
+        }
+      }
+    }
+    if (stv != TT_OK) {
+      hstat[i] = stv;
+      continue;
+    }
+    const double T = p.maturity, K = p.strike, lk = std::log(K);
+    const int N = p.n_grid;
+    const double eta = 2.0 * p.trunc_L / N;
+    const double weight = std::exp(-p.rate * T) * std::pow(eta / (2.0 * M_PI), d);
+    double m[TT_STATIC_MAX_D];
+    for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
+    const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
+    for (int term = 0; term < terms; ++term) {
+      JobDesc jd;
+      std::memset(&jd, 0, sizeof(jd));
+      jd.d = d;
+      jd.n = N;
+      jd.rmax = p.max_rank;
+      jd.instance = i;
+      jd.term = term;
+      jd.param_off = (int)poff;
+      jd.seed = p.seed;
+      jd.T = T;
+      jd.L = p.trunc_L;
+      jd.weight = weight;
+      double* cv = params + poff;
+      double* dl = cv + (size_t)d * d;
+      double* pc = dl + d;
+      double* kd = pc + d;
+      poff += (size_t)d * d + 3 * (size_t)d;
+      if (p.payoff == TT_MIN_CALL) {
+        std::memcpy(cv, p.cov, sizeof(double) * d * d);
+        double sd = 0.0, dm = 0.0, quad = 0.0;
+        for (int j = 0; j < d; ++j) {
+          dl[j] = -p.damping[j];
+          sd += dl[j];
+          dm += dl[j] * m[j];
+          kd[j] = 0.0;
+        }
+        for (int j = 0; j < d; ++j) {
+          double cd = 0.0;
+          for (int l = 0; l < d; ++l) cd += p.cov[j * d + l] * dl[l];
+          pc[j] = m[j] + T * cd;
+          quad += dl[j] * cd;
+        }
+        jd.cauchy = 1;
+        jd.D0 = 1.0 - sd;
+        jd.logscale = lk + dm + 0.5 * T * quad;
+        jd.sign = (d % 2 == 1) ? 1.0 : -1.0;
+      } else {
+        const int j0 = term;
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) {
+            double v = p.cov[a * d + b];
+            if (a != j0) v -= p.cov[j0 * d + b];
+            if (b != j0) v -= p.cov[a * d + j0];
+            if (a != j0 && b != j0) v += p.cov[j0 * d + j0];
+            cv[a * d + b] = v;
+          }
+        double lsc = lk, quad = 0.0;
+        for (int l = 0; l < d; ++l) {
+          dl[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
+          kd[l] = l == j0 ? 1.0 : 0.0;
+        }
+        for (int l = 0; l < d; ++l) {
+          const double mp = l == j0 ? m[j0] : m[l] - m[j0];
+          double cd = 0.0;
+          for (int q = 0; q < d; ++q) cd += cv[l * d + q] * dl[q];
+          pc[l] = mp + T * cd;
+          lsc += dl[l] * mp;
+          quad += dl[l] * cd;
+        }
+        jd.cauchy = 0;
+        jd.D0 = 0.0;
+        jd.logscale = lsc + 0.5 * T * quad;
+        jd.sign = 1.0;
+      }
+      jobs[nj] = jd;
+      ++nj;
+      ++cnt[i];
+    }
+  }
+  // largest jobs first; ties by job number (std::sort works in place)
+  auto cost = [&](int j) {
+    const JobDesc& q = jobs[j];
+    return (double)std::max(q.d - 1, 1) * q.n * (double)q.rmax * q.rmax * (q.d > 1 ? 1.0 : 0.01);
+  };
+  for (int j = 0; j < nj; ++j) order[j] = j;
+  std::sort(order, order + nj, [&](int a, int b) {
+    const double ca = cost(a), cb = cost(b);
+    return ca != cb ? ca > cb : a < b;
+  });
+  h->count = count;
+  h->njobs = nj;
+  size_t off = 0;
+  auto put = [&](size_t src_off, size_t bytes) {
+    const size_t at = off;
+    if (bytes) std::memcpy(h->h_pack + at, h->h_stage + src_off, bytes);
+    off = align_up(off + bytes, 16);
+    return at;
+  };
+  h->p_jobs = put(h->dl.o_jobs, sizeof(JobDesc) * nj);
+  h->p_params = put(h->dl.o_params, sizeof(double) * poff);
+  h->p_order = put(h->dl.o_order, sizeof(int) * nj);
+  h->p_first = put(h->dl.o_first, sizeof(int) * count);
+  h->p_count = put(h->dl.o_count, sizeof(int) * count);
+  h->p_hstatus = put(h->dl.o_hstatus, sizeof(int) * count);
+  h->p_bytes = off;
+  h->last_h2d = off;
+  if (off && cudaMemcpyAsync(h->ws + h->dl.stage, h->h_pack, off, cudaMemcpyHostToDevice,
+                             h->stream) != cudaSuccess)
+    return TT_ERR_CUDA;
+  return TT_OK;
+}
+
+// One-time set-up per device (with that device current): the array's device
+// address and the launch width that fits in it.
+int static_setup(int dev) {
+  StaticDevice& sd = g_static_dev[dev];
+  if (sd.ready) return TT_OK;
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return TT_ERR_CUDA;
+  }
+  for (int prec = 0; prec < 2; ++prec) {
+    Resolved R;
+    tt_options o = static_options(prec, dev, nullptr);
+    if (!resolve(&o, &R)) return TT_ERR_INVALID;
+    const bool f64 = R.o.precision == TT_FP64;
+    SmemLayout S = make_smem(R.o, f64);
+    int grid = 0;
+    const int rc = grid_for(R.o, S, &grid);
+    if (rc != TT_OK) return rc;
+    Layout L = make_layout(R.o, f64);
+    const DevLayout D0 = make_dev_layout(R, L, 0);
+    if (D0.total > TT_STATIC_SCRATCH_BYTES || D0.stage_bytes > kStaticStageBytes) return TT_ERR_CAPACITY;
+    const long long fit = (long long)(TT_STATIC_SCRATCH_BYTES - D0.total) / (long long)L.stride;
+    if (fit < 1) return TT_ERR_CAPACITY;
+    sd.grid[prec] = (int)std::min<long long>(grid, fit);
+  }
+  sd.scratch = reinterpret_cast<char*>(ptr);
+  sd.ready = true;
+  return TT_OK;
+}
+
+}  // namespace
+
+extern "C" int tt_price_evaluate_static(const tt_problem* probs, int count, int precision,
+                                        void* cuda_stream, double* prices, tt_diag* diag) {
+  if (count < 0 || (count > 0 && (!probs || !prices))) return TT_ERR_INVALID;
+  if (count > TT_STATIC_MAX_BATCH) return TT_ERR_CAPACITY;
+  if (precision != TT_FP64 && precision != TT_MIXED) return TT_ERR_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TT_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return TT_ERR_CAPACITY;
+  int rc = static_setup(dev);
+  if (rc != TT_OK) return rc;
+  const StaticDevice& sd = g_static_dev[dev];
+  tt_pricer h;  // on the stack: views of the static arrays, nothing allocated
+  tt_options o = static_options(precision, dev, cuda_stream);
+  if (!resolve(&o, &h.R)) return TT_ERR_INVALID;
+  const bool f64 = h.R.o.precision == TT_FP64;
+  h.lay = make_layout(h.R.o, f64);
+  h.sml = make_smem(h.R.o, f64);
+  h.grid = sd.grid[f64 ? 0 : 1];
+  h.dl = make_dev_layout(h.R, h.lay, h.grid);
+  if (h.dl.total > TT_STATIC_SCRATCH_BYTES || h.dl.stage_bytes > kStaticStageBytes) return TT_ERR_CAPACITY;
+  h.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h.own_ws = false;
+  h.ws = sd.scratch;
+  h.h_stage = reinterpret_cast<char*>(g_static_stage);
+  h.h_pack = reinterpret_cast<char*>(g_static_pack);
+  h.h_ires = g_static_ires;
+  h.count = 0;
+  h.njobs = 0;
+  h.last_h2d = h.last_d2h = 0;
+  rc = prepare_static(&h, probs, count);
+  if (rc != TT_OK) return rc;
+  rc = run_impl(&h);
+  if (rc != TT_OK) return rc;
+  return results_impl(&h, prices, diag);
+}

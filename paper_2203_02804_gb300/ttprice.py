@@ -31,7 +31,13 @@ TT_MIXED = 1
 
 EXPORTS = ("tt_price_create", "tt_workspace_bytes", "tt_price_evaluate", "tt_price_prepare",
            "tt_price_run", "tt_price_results", "tt_price_transfer_bytes", "tt_price_destroy",
-           "tt_status_string")
+           "tt_status_string", "tt_price_evaluate_static")
+
+# limits of tt_price_evaluate_static (include/ttprice.h)
+TT_STATIC_MAX_BATCH = 64
+TT_STATIC_MAX_D = 8
+TT_STATIC_MAX_N = 256
+TT_STATIC_MAX_RANK = 32
 
 
 class tt_options(ctypes.Structure):
@@ -95,6 +101,10 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.tt_price_destroy.restype = None
     lib.tt_status_string.argtypes = [ctypes.c_int]
     lib.tt_status_string.restype = ctypes.c_char_p
+    lib.tt_price_evaluate_static.argtypes = [ctypes.POINTER(tt_problem), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(tt_diag)]
+    lib.tt_price_evaluate_static.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
