@@ -144,6 +144,9 @@ class FourierTensor:
             self.delta = max_call_shift(problem.damping, term)
             self.mu, self.cov = a @ mu, a @ cov @ a.T
         self.scale = math.exp(-problem.rate * problem.maturity) * (self.eta / (2 * math.pi)) ** self.d
+        # spread of TT-cross's random initial pivots (grid steps per axis)
+        from .ttcross import pivot_widths
+        self.pivot_widths = pivot_widths(np.diag(self.cov), float(problem.maturity), self.eta)
 
     def at_points(self, u):
         """Integrand at real points u of shape (..., d)."""

@@ -28,8 +28,10 @@ What the paper fixes (Section IV.A-B) and what is read into it
         price estimate and the sweep stops when two consecutive estimates agree
         to ``sweep_tol`` (relative), or after ``max_half_sweeps``;
       - ranks r_k = min(r_max, N^k, N^(d-k)); initial right sets draw distinct
-        multi-indices with SplitMix64 (slot 0 is the grid centre), or list all
-        N^(d-k) of them in lexicographic order when r_k = N^(d-k).
+        multi-indices with SplitMix64 around the grid centre, with a spread of
+        1.5 standard deviations of the integrand's Gaussian factor per axis
+        (slot 0 is the centre), or list all N^(d-k) of them in lexicographic
+        order when r_k = N^(d-k).
   * Contraction (Section IV.A, MPS inner product): the weights are eta per axis
     (folded into the tensor's scale), so the weighted sum of the train is the
     product of the per-core sums W_k = sum_i G_k[:, i, :].
@@ -74,8 +76,37 @@ def bond_ranks(d, n, r_max):
     return [1] + [min(r_max, n ** k, n ** (d - k)) for k in range(1, d)] + [1]
 
 
-def initial_right_set(d, n, k, size, seed, term):
-    """Distinct right multi-indices over axes k..d-1 (0-based), ``size`` of them."""
+PEAK_ATTEMPTS = 64
+TWO_M53 = 1.0 / 9007199254740992.0  # 2^-53
+SQRT3 = math.sqrt(3.0)
+
+
+def pivot_widths(cov_diag, maturity, eta):
+    """Spread of the initial pivots per axis, in grid steps: 1.5 standard
+    deviations of the Gaussian factor exp(-T/2 Cov_jj u^2), w_j = 1.5/(sqrt(Cov_jj T) eta)."""
+    return [1.5 / (math.sqrt(c * maturity) * eta) for c in cov_diag]
+
+
+def _peak_coordinate(seed, term, k, t, b, j, n, w):
+    """N/2 + round(w z), z ~ (sum of four SplitMix64 uniforms - 2) sqrt(3), clamped."""
+    s = 0.0
+    for q in range(4):
+        s += (splitmix64(pivot_key(seed, term, k, t, b, 4 * j + q)) >> 11) * TWO_M53
+    z = (s - 2.0) * SQRT3
+    idx = n // 2 + math.floor(w * z + 0.5)
+    return min(max(idx, 0), n - 1)
+
+
+def initial_right_set(d, n, k, size, seed, term, widths=None):
+    """Distinct right multi-indices over axes k..d-1 (0-based), ``size`` of them.
+
+    Slot 0 is the grid centre.  The others are random (the paper starts
+    TT-cross from random column sets): the first 64 attempts of a slot draw each
+    coordinate around the centre with spread ``widths[j]`` (where the
+    integrand's Gaussian factor lives); later attempts draw uniformly on the
+    grid.  A draw equal to an earlier slot is rejected.  When r_k = N^(d-k)
+    the set is every multi-index in lexicographic order.
+    """
     width = d - k
     if n ** width == size:
         out = []
@@ -91,7 +122,10 @@ def initial_right_set(d, n, k, size, seed, term):
     seen = {out[0]}
     for b in range(1, size):
         for t in range(65536):
-            cand = tuple(splitmix64(pivot_key(seed, term, k, t, b, j)) % n for j in range(k, d))
+            if widths is not None and t < PEAK_ATTEMPTS:
+                cand = tuple(_peak_coordinate(seed, term, k, t, b, j, n, widths[j]) for j in range(k, d))
+            else:
+                cand = tuple(splitmix64(pivot_key(seed, term, k, t, b, j)) % n for j in range(k, d))
             if cand not in seen:
                 break
         else:
@@ -251,8 +285,9 @@ def tt_cross_sum(tensor, r_max, seed, term=0, opts=None):
     rsets = [None] * (d + 1)
     lsets[0] = [()]
     rsets[d] = [()]
+    widths = getattr(tensor, "pivot_widths", None)
     for k in range(1, d):
-        rsets[k] = initial_right_set(d, n, k, ranks[k], seed, term)
+        rsets[k] = initial_right_set(d, n, k, ranks[k], seed, term, widths)
     diag = CrossDiag()
     prev = None
     est = 0j

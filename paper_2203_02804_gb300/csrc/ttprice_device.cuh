@@ -35,6 +35,11 @@ __device__ __forceinline__ double2 block_sum_d2(double2 v, double* dscr) {
 // ---------------------------------------------------------------------------
 // job set-up: per-axis tables (FP64), their normalisation, initial right sets
 // ---------------------------------------------------------------------------
+// Random initial pivots (the paper starts TT-cross from random column sets):
+// the first kPeakAttempts attempts of a slot draw each coordinate around the
+// grid centre where the integrand's Gaussian factor lives, later ones uniformly.
+constexpr int kPeakAttempts = 64;
+
 // For axis j and grid point u the separable factor is
 //   kind 0:  1/(i u - delta_j)                       * e^{-i p_j u}
 //   kind 1:  1/((i u - delta_j)(1 - delta_j + i u))  * e^{-i p_j u}
@@ -101,8 +106,25 @@ __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, doubl
         uint16_t* dst = rset_at(x, k, b);
         bool fresh = false;
         for (int t = 0; t < 65536 && !fresh; ++t) {
-          for (int pos = 0; pos < width; ++pos)
-            dst[pos] = (uint16_t)(splitmix64(pivot_key(jd.seed, jd.term, k, t, b, k + pos)) % n);
+          for (int pos = 0; pos < width; ++pos) {
+            const int j = k + pos;
+            if (t < kPeakAttempts) {
+              // around the centre, spread w_j = 1.5/(sqrt(Cov_jj T) eta) grid steps; every
+              // operation rounded separately (no contraction) so the draw is reproducible
+              const double w = __ddiv_rn(1.5, __dmul_rn(__dsqrt_rn(__dmul_rn(prm[j * d + j], jd.T)), eta));
+              double sum = 0.0;
+              for (int qq = 0; qq < 4; ++qq) {
+                const unsigned long long h = splitmix64(pivot_key(jd.seed, jd.term, k, t, b, 4 * j + qq));
+                sum = __dadd_rn(sum, __dmul_rn((double)(h >> 11), 0x1p-53));
+              }
+              const double z = __dmul_rn(__dsub_rn(sum, 2.0), 1.7320508075688772);
+              long long idx = n / 2 + (long long)floor(__dadd_rn(__dmul_rn(w, z), 0.5));
+              idx = idx < 0 ? 0 : (idx > n - 1 ? n - 1 : idx);
+              dst[pos] = (uint16_t)idx;
+            } else {
+              dst[pos] = (uint16_t)(splitmix64(pivot_key(jd.seed, jd.term, k, t, b, j)) % n);
+            }
+          }
           fresh = true;
           for (int bb = 0; bb < b && fresh; ++bb) {
             const uint16_t* o = rset_at(x, k, bb);
@@ -275,7 +297,7 @@ __device__ void column_shifts(Ctx<R>& x, int no, int nc) {
 template <typename R>
 __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  cpx<R>* S = x.sw;
+  cpx<R>* __restrict__ S = x.sw;
   for (int c = warp; c < ncol; c += kWarps) {
     R mx = 0;
     for (int r = lane; r < q; r += 32) mx = fmax(mx, cabs2(S[c * ld + r]));
@@ -291,7 +313,7 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
   int buf = 0;
   block_argmax(v, vi, x.redv, x.redi, buf);
   int nsel = 0;
-  double fl = 0.0;
+  long long fl = 0;  // complex multiply-adds (thread 0's count is used)
   for (int c = 0; c < ncol; ++c) {
     const int p = vi;
     const bool take = (v > thr2 * x.colmax[c]) && (v > R(0));
@@ -304,10 +326,27 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
       if (tid == p) mine_used = true;
       if (active && c + 1 < ncol) {
         const cpx<R> l = cmul(S[c * ld + tid], crecip(S[c * ld + p]));
-        for (int j = c + 1; j < ncol; ++j) cfms(S[j * ld + tid], l, S[j * ld + p]);
+        // four columns at a time: loads first, then the updates, so the loads
+        // of a chunk do not wait on the previous chunk's stores
+        int j = c + 1;
+        for (; j + 3 < ncol; j += 4) {
+          cpx<R> a0 = S[j * ld + tid], a1 = S[(j + 1) * ld + tid];
+          cpx<R> a2 = S[(j + 2) * ld + tid], a3 = S[(j + 3) * ld + tid];
+          const cpx<R> p0 = S[j * ld + p], p1 = S[(j + 1) * ld + p];
+          const cpx<R> p2 = S[(j + 2) * ld + p], p3 = S[(j + 3) * ld + p];
+          cfms(a0, l, p0);
+          cfms(a1, l, p1);
+          cfms(a2, l, p2);
+          cfms(a3, l, p3);
+          S[j * ld + tid] = a0;
+          S[(j + 1) * ld + tid] = a1;
+          S[(j + 2) * ld + tid] = a2;
+          S[(j + 3) * ld + tid] = a3;
+        }
+        for (; j < ncol; ++j) cfms(S[j * ld + tid], l, S[j * ld + p]);
       }
       ++nsel;
-      fl += 8.0 * (double)(q - nsel) * (double)(ncol - c - 1);
+      if (tid == 0) fl += (long long)(q - nsel) * (ncol - c - 1);
     }
     if (c + 1 < ncol) {
       const bool active = own && !mine_used;
@@ -317,7 +356,7 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
       block_argmax(v, vi, x.redv, x.redi, buf);
     }
   }
-  if (tid == 0) x.flops += fl;
+  if (tid == 0) x.flops += 8.0 * (double)fl;
   __syncthreads();
   return nsel;
 }
@@ -412,10 +451,27 @@ __device__ int tournament(Ctx<R>& x, int m, int nc, int b, R thr2) {
       const int t = idx % rho, c = idx / rho;
       x.sw[c * ldq + t] = x.wvals[c * x.rall + t];
     }
-    for (int idx = tid; idx < bs * nc; idx += kThreads) {
-      const int r = idx % bs, c = idx / bs;
-      const int g = rs + r;
-      x.sw[c * ldq + rho + r] = eval_point(x, g / N, g % N, c);
+    {
+      // four independent evaluations per thread and iteration (loads before stores)
+      const int tot = bs * nc;
+      for (int base = tid; base < tot; base += 4 * kThreads) {
+        cpx<R> v[4];
+        int dst[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = base + u * kThreads;
+          dst[u] = -1;
+          if (idx < tot) {
+            const int r = idx % bs, c = idx / bs;
+            const int g = rs + r;
+            v[u] = eval_point(x, g / N, g % N, c);
+            dst[u] = c * ldq + rho + r;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (dst[u] >= 0) x.sw[dst[u]] = v[u];
+      }
     }
     if (tid == 0) x.flops += 24.0 * bs * nc;
     __syncthreads();
@@ -492,10 +548,26 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
     cpx<R>* A = x.sw;  // bs x rho, column-major, leading dimension b
     // stage_pairs needs the kept columns' entries: stage all columns up to the largest kept one
     stage_pairs(x, rs / N, (rs + bs - 1) / N, x.jp[rho - 1] + 1);
-    for (int idx = tid; idx < bs * rho; idx += kThreads) {
-      const int r = idx % bs, t = idx / bs;
-      const int g = rs + r;
-      A[t * b + r] = eval_point(x, g / N, g % N, x.jp[t]);
+    {
+      const int tot = bs * rho;
+      for (int base = tid; base < tot; base += 4 * kThreads) {
+        cpx<R> v[4];
+        int dst[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = base + u * kThreads;
+          dst[u] = -1;
+          if (idx < tot) {
+            const int r = idx % bs, t = idx / bs;
+            const int g = rs + r;
+            v[u] = eval_point(x, g / N, g % N, x.jp[t]);
+            dst[u] = t * b + r;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (dst[u] >= 0) A[dst[u]] = v[u];
+      }
     }
     if (tid == 0) x.flops += 24.0 * bs * rho + 8.0 * (double)bs * rho * rho;
     __syncthreads();

@@ -74,15 +74,24 @@ __device__ __forceinline__ R cabs2(cpx<R> a) {
   return a.re * a.re + a.im * a.im;
 }
 // 1/a by Smith's method (Smith 1962): no squares of the operands, so it stays
-// finite for any nonzero a in range.
+// finite for any nonzero a in range.  FP32 uses the fast reciprocal (its error
+// is a few ulp, far below the path's 1e-4 target).
+template <typename R>
+__device__ __forceinline__ R fast_rcp(R v) {
+  if constexpr (sizeof(R) == 4) {
+    return __fdividef(R(1), v);
+  } else {
+    return R(1) / v;
+  }
+}
 template <typename R>
 __device__ __forceinline__ cpx<R> crecip(cpx<R> a) {
   if (fabs(a.re) >= fabs(a.im)) {
-    const R r = a.im / a.re, den = a.re + a.im * r;
-    return {R(1) / den, -r / den};
+    const R r = a.im * fast_rcp(a.re), inv = fast_rcp(a.re + a.im * r);
+    return {inv, -r * inv};
   }
-  const R r = a.re / a.im, den = a.re * r + a.im;
-  return {r / den, R(-1) / den};
+  const R r = a.re * fast_rcp(a.im), inv = fast_rcp(a.re * r + a.im);
+  return {r * inv, -inv};
 }
 
 // exp of the log-magnitude: FP32 tables hold E in log2 units, FP64 in natural units.
