@@ -13,10 +13,13 @@ What the paper fixes (Section IV.A-B) and what is read into it
       - core k's fiber matrix A has rows (outer multi-index o, grid index i),
         row number o*N + i, and the opposite index set as columns;
       - initial rows: Gaussian elimination with partial pivoting (GEPP) run as a
-        flat tournament over blocks of ``block_rows`` rows: the current winners
-        are stacked on top of the next block and GEPP keeps the pivot rows.  A
-        column whose best pivot is at most ``theta`` times that column's largest
-        entry is skipped (numerically dependent); the kept columns set the rank;
+        flat tournament: the current winners are stacked on top of the next
+        candidates and GEPP keeps the pivot rows.  Candidates are the next block
+        of ``block_rows`` rows for fibers of at most 256 rows; larger fibers are
+        screened in blocks of 512 rows, each 64-row sub-block offering its 16
+        rows with the largest entries.  A column whose best pivot is at most
+        ``theta`` times that column's largest entry is skipped (numerically
+        dependent); the kept columns set the rank;
       - maxvol: B = A_c A_c[W]^{-1} on the kept columns, blocks visited
         cyclically; inside a block, while max |B_ij| > 1 + tau swap row i into
         slot j (rank-one update of B, at most rank-many swaps per block); stop
@@ -171,12 +174,39 @@ def gepp_select(c_mat, theta):
     return rows, cols
 
 
+SCREEN_MIN_ROWS = 256   # fibers with more rows than this are screened
+SCREEN_BLOCK = 512      # rows per screening block (one GEPP merge each)
+SCREEN_SUB = 64         # rows per sub-block
+SCREEN_KEEP = 16        # rows each sub-block keeps
+
+
+def screen_rows(a_mat, start, stop):
+    """Candidates of one screening block: in every 64-row sub-block, the 16 rows
+    whose largest |entry|^2 (over all columns, rounded to FP32) is largest, ties
+    to the lower row; returned in ascending row order."""
+    keys = (a_mat[start:stop].real ** 2 + a_mat[start:stop].imag ** 2).max(axis=1).astype(np.float32)
+    kept = []
+    for s0 in range(0, stop - start, SCREEN_SUB):
+        sub = list(range(s0, min(stop - start, s0 + SCREEN_SUB)))
+        best = sorted(sub, key=lambda r: (-float(keys[r]), r))[:SCREEN_KEEP]
+        kept += [start + r for r in sorted(best)]
+    return kept
+
+
 def tournament_select(a_mat, block_rows, theta):
-    """Flat GEPP tournament over row blocks; returns (winner rows, kept columns)."""
+    """Flat GEPP tournament; returns (winner rows, kept columns).
+
+    Each merge runs GEPP on the current winners stacked on top of new
+    candidates: the next block of ``block_rows`` rows when the fiber has at most
+    SCREEN_MIN_ROWS rows, else the screened rows of the next SCREEN_BLOCK rows.
+    """
     m = a_mat.shape[0]
     winners, cols = [], []
-    for start in range(0, m, block_rows):
-        cand = winners + list(range(start, min(m, start + block_rows)))
+    step = block_rows if m <= SCREEN_MIN_ROWS else SCREEN_BLOCK
+    for start in range(0, m, step):
+        stop = min(m, start + step)
+        fresh = list(range(start, stop)) if m <= SCREEN_MIN_ROWS else screen_rows(a_mat, start, stop)
+        cand = winners + fresh
         r, c = gepp_select(a_mat[cand, :], theta)
         winners = [cand[p] for p in r]
         cols = c

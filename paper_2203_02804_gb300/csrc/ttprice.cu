@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
   x.jp = reinterpret_cast<int*>(smem + sl.jp);
   x.selr = reinterpret_cast<int*>(smem + sl.selr);
   x.selc = reinterpret_cast<int*>(smem + sl.selc);
+  x.scand = reinterpret_cast<int*>(smem + sl.scand);
+  x.scnt = reinterpret_cast<int*>(smem + sl.scnt);
   x.redv = reinterpret_cast<R*>(smem + sl.redv);
   x.redi = reinterpret_cast<int*>(smem + sl.redi);
   x.swcol = reinterpret_cast<cpx<R>*>(smem + sl.swcol);
@@ -320,7 +322,7 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   SmemLayout S;
   const int rs = f64 ? 8 : 4, cs = 2 * rs;
   const int r = o.max_rank, b = o.block_rows, n = o.max_n, d = o.max_d;
-  int sw_elems = std::max((r + b) * r, 2 * r * r);
+  int sw_elems = std::max((r + std::max(b, 128)) * r, 2 * r * r);
   sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + cs - 1) / cs);
   int off = 0;
   auto take = [&](int bytes) {
@@ -341,6 +343,8 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   S.jp = take(r * 4);
   S.selr = take(r * 4);
   S.selc = take(r * 4);
+  S.scand = take(ttp::kThreads * 4);
+  S.scnt = take(ttp::kWarps * 4);
   S.redv = take(2 * ttp::kWarps * rs);
   S.redi = take(2 * ttp::kWarps * 4);
   S.redk = take(2 * ttp::kWarps * 4);

@@ -435,18 +435,90 @@ __device__ __forceinline__ void eval_prow(Ctx<R>& x, int j, int g, int rho) {
 // The winners' original rows are cached in wvals (column-major, ld rall), so a
 // merge evaluates only its block and the block rows that win.
 // ---------------------------------------------------------------------------
+// Fibers of more than kScreenMinRows rows are screened: every kScreenBlock rows
+// form one merge, whose candidates are, from each kScreenSub-row sub-block, the
+// kScreenKeep rows with the largest max_c |a_rc|^2 (rounded to FP32; ties to the
+// lower row), in ascending row order.  One warp screens one sub-block.
+constexpr int kScreenMinRows = 256;
+constexpr int kScreenBlock = 512;
+constexpr int kScreenSub = 64;
+constexpr int kScreenKeep = 16;
+
+template <typename R>
+__device__ int screen_block(Ctx<R>& x, int ss, int se, int nc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = x.n;
+  const int base = ss + warp * kScreenSub;
+  float key[2];
+  bool valid[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = base + lane + 32 * h;
+    valid[h] = r < se;
+    key[h] = 0.0f;
+    if (valid[h]) {
+      R mx = R(0);
+      for (int c = 0; c < nc; ++c) mx = fmax(mx, cabs2(eval_point_unscaled(x, r / N, r % N, c)));
+      key[h] = (float)mx;
+    }
+  }
+  // warp top-kScreenKeep: repeated argmax; the kept set is a 64-bit row mask
+  unsigned long long kept = 0ull;
+  bool taken[2] = {false, false};
+  for (int t = 0; t < kScreenKeep; ++t) {
+    float v = -1.0f;
+    int vi = INT_MAX;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (valid[h] && !taken[h]) am_merge(v, vi, key[h], lane + 32 * h);
+    warp_argmax(v, vi);
+    if (vi == INT_MAX) break;
+    kept |= 1ull << vi;
+    if ((vi & 31) == lane) taken[vi >> 5] = true;
+  }
+  // write the kept rows of this sub-block in ascending order
+  const int cnt = __popcll(kept);
+  if (lane < cnt) {
+    unsigned long long msk = kept;
+    for (int q = 0; q < lane; ++q) msk &= msk - 1ull;  // drop the lane lowest set bits
+    x.scand[warp * kScreenKeep + lane] = base + __ffsll((long long)msk) - 1;
+  }
+  if (lane == 0) x.scnt[warp] = cnt;
+  __syncthreads();
+  // compact the per-warp lists (warp order = row order)
+  int tot = 0;
+  for (int w = 0; w < kWarps; ++w) tot += x.scnt[w];
+  int out = 0, sel = -1;
+  for (int w = 0; w < kWarps; ++w) {
+    if (tid >= out && tid < out + x.scnt[w]) sel = x.scand[w * kScreenKeep + (tid - out)];
+    out += x.scnt[w];
+  }
+  __syncthreads();
+  if (sel >= 0) x.scand[tid] = sel;
+  if (tid == 0) x.flops += 24.0 * (double)(se - ss) * nc;
+  __syncthreads();
+  return tot;
+}
+
 template <typename R>
 __device__ int tournament(Ctx<R>& x, int m, int nc, int b, R thr2) {
   const int tid = threadIdx.x, N = x.n;
-  const int nb = (m + b - 1) / b;
-  const int ldq = x.rall + b;
+  const bool screened = m > kScreenMinRows;
+  const int step = screened ? kScreenBlock : b;
+  const int nb = (m + step - 1) / step;
+  const int ldq = x.rall + max(b, kWarps * kScreenKeep);
   int rho = 0;
   for (int beta = 0; beta < nb; ++beta) {
-    const int rs = beta * b;
-    const int bs = min(b, m - rs);
-    const int q = rho + bs;
+    const int rs = beta * step;
+    const int bs0 = min(step, m - rs);
     TTP_TIC(t_ev);
-    stage_pairs(x, rs / N, (rs + bs - 1) / N, nc);
+    int bs = bs0;
+    if (screened) {
+      stage_pairs(x, 0, -1, nc);  // screening reads pair entries from global memory
+      bs = screen_block(x, rs, rs + bs0, nc);
+    } else {
+      stage_pairs(x, rs / N, (rs + bs0 - 1) / N, nc);
+    }
+    const int q = rho + bs;
     for (int idx = tid; idx < rho * nc; idx += kThreads) {
       const int t = idx % rho, c = idx / rho;
       x.sw[c * ldq + t] = x.wvals[c * x.rall + t];
@@ -463,7 +535,7 @@ __device__ int tournament(Ctx<R>& x, int m, int nc, int b, R thr2) {
           dst[u] = -1;
           if (idx < tot) {
             const int r = idx % bs, c = idx / bs;
-            const int g = rs + r;
+            const int g = screened ? x.scand[r] : rs + r;
             v[u] = eval_point(x, g / N, g % N, c);
             dst[u] = c * ldq + rho + r;
           }
@@ -488,14 +560,14 @@ __device__ int tournament(Ctx<R>& x, int m, int nc, int b, R thr2) {
       if (cr < rho) {
         v = x.wvals[c * x.rall + cr];
       } else {
-        const int g = rs + cr - rho;
+        const int g = screened ? x.scand[cr - rho] : rs + cr - rho;
         v = eval_point(x, g / N, g % N, c);
       }
       x.sw[c * x.rall + t] = v;
     }
     for (int t = tid; t < nsel; t += kThreads) {
       const int cr = x.selr[t];
-      x.wnew[t] = cr < rho ? x.wrow[cr] : rs + cr - rho;
+      x.wnew[t] = cr < rho ? x.wrow[cr] : (screened ? x.scand[cr - rho] : rs + cr - rho);
     }
     __syncthreads();
     for (int idx = tid; idx < nsel * nc; idx += kThreads) {

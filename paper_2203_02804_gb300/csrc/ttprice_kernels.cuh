@@ -153,7 +153,7 @@ struct Layout {
 
 // shared-memory carve, byte offsets (sizes depend on R)
 struct SmemLayout {
-  int sw, m, wvals, stage, tab, colmax, cshift, wrow, wnew, jp, selr, selc, redv, redi, redk, swcol,
+  int sw, m, wvals, stage, tab, colmax, cshift, wrow, wnew, jp, selr, selc, scand, scnt, redv, redi, redk, swcol,
       swrow, mcol, lsz, rsz, misc, total;
   int sw_elems;
 };
@@ -287,6 +287,8 @@ struct Ctx {
   int* jp;
   int* selr;
   int* selc;
+  int* scand;  // screened candidate rows [kWarps * 16]
+  int* scnt;   // per-warp kept counts [kWarps]
   R* redv;
   int* redi;
   unsigned* redk;
@@ -328,14 +330,14 @@ __device__ __forceinline__ R eval_logmag(const Ctx<R>& x, int o, int i, int col)
 }
 
 // ---------------------------------------------------------------------------
-// integrand at one fiber point
+// integrand at one fiber point (Scaled: with the FP32 column shift)
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool Scaled = true>
 __device__ __forceinline__ cpx<R> eval_point(const Ctx<R>& x, int o, int i, int col) {
   const PairE<R> q = pair_at(x, o, col);
   const R ui = x.tu[i];
   R e = q.e0 + x.tl[i] + q.h * ui;
-  if constexpr (Num<R>::kScaleColumns) e -= x.cshift[col];
+  if constexpr (Num<R>::kScaleColumns && Scaled) e -= x.cshift[col];
   cpx<R> w = cmul(cpx<R>{q.ore, q.oim}, cpx<R>{x.tor[i], x.toi[i]});
   R f = Num<R>::ex(e);
   if (x.cauchy) {
@@ -345,6 +347,11 @@ __device__ __forceinline__ cpx<R> eval_point(const Ctx<R>& x, int o, int i, int 
     w = cmul(w, cpx<R>{x.D0, -s});
   }
   return {w.re * f, w.im * f};
+}
+
+template <typename R>
+__device__ __forceinline__ cpx<R> eval_point_unscaled(const Ctx<R>& x, int o, int i, int col) {
+  return eval_point<R, false>(x, o, i, col);
 }
 
 }  // namespace ttp
