@@ -60,7 +60,7 @@ typedef struct {
   int max_batch;        /* largest number of problems per evaluate call            */
   tt_precision precision;
   int max_half_sweeps;  /* 0 -> 8 (alternating left-to-right / right-to-left)       */
-  double sweep_tol;     /* <= 0 -> 1e-7 (FP64) or 1e-5 (mixed): relative change of
+  double sweep_tol;     /* <= 0 -> 1e-6 (FP64) or 1e-5 (mixed): relative change of
                            the price estimate between half-sweeps that stops a job */
   double rank_tol;      /* <= 0 -> 1e-8 (FP64) or 1e-5 (mixed): a column whose
                            elimination pivot is below rank_tol times the column's

@@ -55,7 +55,7 @@ class CrossOptions:
     theta: float = 1e-8           # relative pivot threshold for skipping a column
     tau: float = 0.05             # maxvol tolerance: stop when |B| <= 1 + tau
     max_half_sweeps: int = 8
-    sweep_tol: float = 1e-7
+    sweep_tol: float = 1e-6
 
 
 @dataclass

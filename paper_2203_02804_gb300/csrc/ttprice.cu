@@ -270,7 +270,7 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.max_half_sweeps == 0) o.max_half_sweeps = 8;
   if (o.max_half_sweeps < 1 || o.max_half_sweeps > 1000) return false;
   const bool f64 = o.precision == TT_FP64;
-  if (!(o.sweep_tol > 0)) o.sweep_tol = f64 ? 1e-7 : 1e-5;
+  if (!(o.sweep_tol > 0)) o.sweep_tol = f64 ? 1e-6 : 1e-5;
   if (!(o.rank_tol > 0)) o.rank_tol = f64 ? 1e-8 : 1e-5;
   if (!(o.maxvol_tol > 0)) o.maxvol_tol = 0.05;
   if (!std::isfinite(o.sweep_tol) || !std::isfinite(o.rank_tol) || !std::isfinite(o.maxvol_tol))
@@ -1129,3 +1129,17 @@ extern "C" int tt_price_evaluate_static(const tt_problem* probs, int count, int 
   if (rc != TT_OK) return rc;
   return results_impl(&h, prices, diag);
 }
+
+#ifdef TTP_PHASE_TIMERS
+// Profiling builds only (not part of the ABI in include/ttprice.h): read and
+// optionally clear the per-phase cycle counters of the current device.
+extern "C" int tt_phase_cycles(unsigned long long* out16, int reset) {
+  if (out16 && cudaMemcpyFromSymbol(out16, ttp::g_phase_cycles, 16 * sizeof(unsigned long long)) != cudaSuccess)
+    return TT_ERR_CUDA;
+  if (reset) {
+    const unsigned long long z[16] = {0};
+    if (cudaMemcpyToSymbol(ttp::g_phase_cycles, z, sizeof(z)) != cudaSuccess) return TT_ERR_CUDA;
+  }
+  return TT_OK;
+}
+#endif

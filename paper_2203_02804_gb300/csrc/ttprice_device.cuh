@@ -620,31 +620,25 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
     cpx<R>* A = x.sw;  // bs x rho, column-major, leading dimension b
     // stage_pairs needs the kept columns' entries: stage all columns up to the largest kept one
     stage_pairs(x, rs / N, (rs + bs - 1) / N, x.jp[rho - 1] + 1);
-    {
-      const int tot = bs * rho;
-      for (int base = tid; base < tot; base += 4 * kThreads) {
-        cpx<R> v[4];
-        int dst[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int idx = base + u * kThreads;
-          dst[u] = -1;
-          if (idx < tot) {
-            const int r = idx % bs, t = idx / bs;
-            const int g = rs + r;
-            v[u] = eval_point(x, g / N, g % N, x.jp[t]);
-            dst[u] = t * b + r;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (dst[u] >= 0) A[dst[u]] = v[u];
-      }
+    // rows of this block that are pivots already: their B rows are unit vectors,
+    // never maxvol candidates (excluding them only guards against FP32 drift)
+    unsigned char* inw = reinterpret_cast<unsigned char*>(x.scand);
+    for (int r = tid; r < bs; r += kThreads) inw[r] = 0;
+    // two threads per row (128 rows per pass), each the row's every other kept column
+    for (int rr = tid & 127; rr < bs; rr += 128) {
+      const int g = rs + rr;
+      const RowTab<R> rt = row_tab(x, g % N);
+      const int o = g / N;
+      for (int t = tid >> 7; t < rho; t += 2) A[t * b + rr] = eval_row_point(x, rt, o, x.jp[t]);
     }
     if (tid == 0) x.flops += 24.0 * bs * rho + 8.0 * (double)bs * rho * rho;
     __syncthreads();
     TTP_TOC(t_rev, 6);
     TTP_TIC(t_gemm);
+    for (int t = tid; t < rho; t += kThreads) {
+      const int g = x.wrow[t] - rs;
+      if (g >= 0 && g < bs) inw[g] = 1;
+    }
     if (visits < nb) {  // first cycle: row sums over i per outer index
       const int olo = rs / N, ohi = (rs + bs - 1) / N;
       const int nol = ohi - olo + 1;
@@ -701,7 +695,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
             const int r = r0 + rt + a * rtiles, cc = col0 + c;
             if (r < bs && cc < rho) {
               A[cc * b + r] = acc[a][c];
-              am_merge(bv, bi, cabs2(acc[a][c]), r * rho + cc);
+              if (!inw[r]) am_merge(bv, bi, cabs2(acc[a][c]), r * rho + cc);
             }
           }
       }
@@ -719,7 +713,12 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
         x.swrow[t] = A[t * b + i];
         x.mcol[t] = x.M[t * x.rall + j];
       }
-      if (tid == 0) x.wrow[j] = rs + i;
+      if (tid == 0) {
+        const int old = x.wrow[j] - rs;
+        if (old >= 0 && old < bs) inw[old] = 0;
+        inw[i] = 1;
+        x.wrow[j] = rs + i;
+      }
       __syncthreads();
       eval_prow(x, j, rs + i, rho);
       const cpx<R> ipiv = crecip(x.swrow[j]);
@@ -732,7 +731,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
         cpx<R> bb = A[t * b + r];
         cfms(bb, x.swcol[r], cmul(rv, ipiv));
         A[t * b + r] = bb;
-        am_merge(bv, bi, cabs2(bb), r * rho + t);
+        if (!inw[r]) am_merge(bv, bi, cabs2(bb), r * rho + t);
       }
       for (int idx = tid; idx < rho * rho; idx += kThreads) {
         const int r = idx / rho, t = idx % rho;
@@ -775,6 +774,7 @@ __device__ void chain_solve(Ctx<R>& x, int no, int rho) {
     x.ychain[t] = y;
   }
   __syncthreads();
+  // Gaussian elimination with partial pivoting on P^T, FP64
   double2* G = reinterpret_cast<double2*>(x.sw);  // rho x (rho+1), row-major
   const int lg = rho + 1;
   for (int idx = tid; idx < rho * lg; idx += kThreads) {

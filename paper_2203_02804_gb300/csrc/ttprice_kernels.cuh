@@ -349,6 +349,31 @@ __device__ __forceinline__ cpx<R> eval_point(const Ctx<R>& x, int o, int i, int 
   return {w.re * f, w.im * f};
 }
 
+// the grid-index part of a fiber point, loaded once per row
+template <typename R>
+struct RowTab {
+  R l, u, re, im;
+};
+template <typename R>
+__device__ __forceinline__ RowTab<R> row_tab(const Ctx<R>& x, int i) {
+  return {x.tl[i], x.tu[i], x.tor[i], x.toi[i]};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> eval_row_point(const Ctx<R>& x, const RowTab<R>& rt, int o, int col) {
+  const PairE<R> q = pair_at(x, o, col);
+  R e = q.e0 + rt.l + q.h * rt.u;
+  if constexpr (Num<R>::kScaleColumns) e -= x.cshift[col];
+  cpx<R> w = cmul(cpx<R>{q.ore, q.oim}, cpx<R>{rt.re, rt.im});
+  R f = Num<R>::ex(e);
+  if (x.cauchy) {
+    const R s = q.s0 + rt.u;
+    const R den = fma(s, s, x.D0 * x.D0);
+    f = Num<R>::div(f, den);
+    w = cmul(w, cpx<R>{x.D0, -s});
+  }
+  return {w.re * f, w.im * f};
+}
+
 template <typename R>
 __device__ __forceinline__ cpx<R> eval_point_unscaled(const Ctx<R>& x, int o, int i, int col) {
   return eval_point<R, false>(x, o, i, col);
