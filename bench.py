@@ -38,9 +38,22 @@ FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.
 
 
 def workload_problems(batch, rank_offset=0):
+    """The batch priced by one rank: rank r draws its own seeded problems
+    (weak scaling: every rank prices `batch` problems; no data is exchanged)."""
     from paper_2203_02804_gb300 import inputs
 
     return inputs.five_asset_batch(batch, index=1 + 10 * rank_offset)
+
+
+def max_over_ranks(value, dist):
+    """Largest value over the ranks (the job's time is its slowest rank's)."""
+    import torch
+
+    if dist is None:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload_config(batch, precision="mixed"):
@@ -215,11 +228,7 @@ def run_gpu(args):
             ev[s][1].record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist)
     rc, prices, diags = pr.results()
     flops_per_step = sum(d.flops for d in diags)
     evals_per_step = sum(d.evaluations for d in diags)
@@ -235,10 +244,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     h2d, d2h = pr.transfer_bytes()
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     e2e_value = args.batch * world * args.steps / e2e_s
     pr.close()
 

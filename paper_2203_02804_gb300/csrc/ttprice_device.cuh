@@ -367,7 +367,7 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
 template <typename R>
 __device__ void invert_pivots(Ctx<R>& x, int rho) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ld = 2 * rho;
+  const int w2 = 2 * rho, ld = w2 + 1;  // odd row stride: column accesses are conflict-free
   cpx<R>* G = x.sw;
   for (int idx = tid; idx < rho * rho; idx += kThreads) {
     const int r = idx / rho, c = idx % rho;
@@ -392,7 +392,7 @@ __device__ void invert_pivots(Ctx<R>& x, int rho) {
     __syncthreads();
     const int p = x.misc[MISC_PIV];
     if (p != c && p < rho) {
-      for (int j = tid; j < ld; j += kThreads) {
+      for (int j = tid; j < w2; j += kThreads) {
         const cpx<R> t = G[c * ld + j];
         G[c * ld + j] = G[p * ld + j];
         G[p * ld + j] = t;
@@ -401,14 +401,14 @@ __device__ void invert_pivots(Ctx<R>& x, int rho) {
     __syncthreads();
     const cpx<R> inv = crecip(G[c * ld + c]);
     for (int r = tid; r < rho; r += kThreads) x.swcol[r] = G[r * ld + c];
-    for (int j = tid; j < ld; j += kThreads) x.swrow[j] = cmul(G[c * ld + j], inv);
+    for (int j = tid; j < w2; j += kThreads) x.swrow[j] = cmul(G[c * ld + j], inv);
     __syncthreads();
-    for (int idx = tid; idx < rho * ld; idx += kThreads) {
-      const int r = idx / ld, j = idx % ld;
+    for (int idx = tid; idx < rho * w2; idx += kThreads) {
+      const int r = idx / w2, j = idx % w2;
       if (r == c) {
-        G[idx] = x.swrow[j];
+        G[r * ld + j] = x.swrow[j];
       } else {
-        cfms(G[idx], x.swcol[r], x.swrow[j]);
+        cfms(G[r * ld + j], x.swcol[r], x.swrow[j]);
       }
     }
     __syncthreads();
@@ -640,21 +640,33 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       if (g >= 0 && g < bs) inw[g] = 1;
     }
     if (visits < nb) {  // first cycle: row sums over i per outer index
+      // one warp per (outer index, kept column); lanes take consecutive rows
+      // (conflict-free), compensated (Kahan) partial sums, then a fixed-order
+      // warp reduction, added to the FP64 accumulator
+      const int lane = tid & 31, warp = tid >> 5;
       const int olo = rs / N, ohi = (rs + bs - 1) / N;
       const int nol = ohi - olo + 1;
-      for (int idx = tid; idx < nol * rho; idx += kThreads) {
-        const int ol = idx % nol, t = idx / nol;
+      for (int pr = warp; pr < nol * rho; pr += kWarps) {
+        const int ol = pr % nol, t = pr / nol;
         const int o = olo + ol;
         const int r0 = max(o * N, rs) - rs, r1 = min(o * N + N, rs + bs) - rs;
-        R sr = 0, si = 0, cr = 0, ci = 0;  // compensated (Kahan) sums
-        for (int r = r0; r < r1; ++r) {
+        R sr = 0, si = 0, cr = 0, ci = 0;
+        for (int r = r0 + lane; r < r1; r += 32) {
           const cpx<R> a = A[t * b + r];
           R y = a.re - cr; R s2 = sr + y; cr = (s2 - sr) - y; sr = s2;
           y = a.im - ci; s2 = si + y; ci = (s2 - si) - y; si = s2;
         }
-        double2& acc = x.sacc[o * x.rall + t];
-        acc.x += (double)sr;
-        acc.y += (double)si;
+        R vr = sr - cr, vi = si - ci;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          vr += __shfl_xor_sync(0xffffffffu, vr, off);
+          vi += __shfl_xor_sync(0xffffffffu, vi, off);
+        }
+        if (lane == 0) {
+          double2& acc = x.sacc[o * x.rall + t];
+          acc.x += (double)vr;
+          acc.y += (double)vi;
+        }
       }
     }
     // B = A M in row strips; each strip is read completely before it is overwritten
