@@ -60,8 +60,9 @@ typedef struct {
   int max_batch;        /* largest number of problems per evaluate call            */
   tt_precision precision;
   int max_half_sweeps;  /* 0 -> 8 (alternating left-to-right / right-to-left)       */
-  double sweep_tol;     /* <= 0 -> 1e-6 (FP64) or 1e-5 (mixed): relative change of
-                           the price estimate between half-sweeps that stops a job */
+  double sweep_tol;     /* <= 0 -> 1e-6 (FP64) or 1e-4 (mixed): relative change of
+                           the price estimate between half-sweeps that stops a job
+                           (each path's accuracy target against the FP64 oracle)  */
   double rank_tol;      /* <= 0 -> 1e-8 (FP64) or 1e-5 (mixed): a column whose
                            elimination pivot is below rank_tol times the column's
                            largest entry is dropped (numerically dependent)        */

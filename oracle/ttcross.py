@@ -177,7 +177,7 @@ def gepp_select(c_mat, theta):
 SCREEN_MIN_ROWS = 256   # fibers with more rows than this are screened
 SCREEN_BLOCK = 512      # rows per screening block (one GEPP merge each)
 SCREEN_SUB = 64         # rows per sub-block
-SCREEN_KEEP = 16        # rows each sub-block keeps
+SCREEN_KEEP = 16        # rows each sub-block keeps (a fiber of more than 256 rows offers >= 64)
 
 
 def screen_rows(a_mat, start, stop):

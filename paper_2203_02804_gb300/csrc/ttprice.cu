@@ -270,7 +270,7 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.max_half_sweeps == 0) o.max_half_sweeps = 8;
   if (o.max_half_sweeps < 1 || o.max_half_sweeps > 1000) return false;
   const bool f64 = o.precision == TT_FP64;
-  if (!(o.sweep_tol > 0)) o.sweep_tol = f64 ? 1e-6 : 1e-5;
+  if (!(o.sweep_tol > 0)) o.sweep_tol = f64 ? 1e-6 : 1e-4;
   if (!(o.rank_tol > 0)) o.rank_tol = f64 ? 1e-8 : 1e-5;
   if (!(o.maxvol_tol > 0)) o.maxvol_tol = 0.05;
   if (!std::isfinite(o.sweep_tol) || !std::isfinite(o.rank_tol) || !std::isfinite(o.maxvol_tol))

@@ -129,32 +129,51 @@ class Diag:
     flops: float
 
 
+# tt_problem as a NumPy record (same offsets as the C struct; checked by the tests)
+PROBLEM_DTYPE = np.dtype({
+    "names": ["d", "spot", "cov", "rate", "maturity", "strike", "payoff", "damping", "n_grid",
+              "trunc_L", "max_rank", "seed"],
+    "formats": [np.int32, np.uint64, np.uint64, np.float64, np.float64, np.float64, np.int32,
+                np.uint64, np.int32, np.float64, np.int32, np.uint64],
+    "offsets": [0, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 88],
+    "itemsize": 96,
+})
+
+
 class ProblemBatch:
-    """Host arrays of a batch, kept alive for the duration of the C calls."""
+    """Host arrays of a batch in the C layout, kept alive for the duration of the C calls.
+
+    The per-problem vectors are packed into three contiguous FP64 arrays and the
+    tt_problem records are filled column-wise with NumPy.
+    """
 
     def __init__(self, problems: Sequence):
-        self.keep = []
-        self.arr = (tt_problem * max(1, len(problems)))()
-        dbl = ctypes.POINTER(ctypes.c_double)
-        for i, p in enumerate(problems):
-            spot = np.ascontiguousarray(p.spot, dtype=np.float64)
-            cov = np.ascontiguousarray(p.cov, dtype=np.float64)
-            damp = np.ascontiguousarray(p.damping, dtype=np.float64)
-            self.keep += [spot, cov, damp]
-            s = self.arr[i]
-            s.d = int(spot.size)
-            s.spot = spot.ctypes.data_as(dbl)
-            s.cov = cov.ctypes.data_as(dbl)
-            s.rate = float(p.rate)
-            s.maturity = float(p.maturity)
-            s.strike = float(p.strike)
-            s.payoff = TT_MIN_CALL if p.payoff == "min" else TT_MAX_CALL
-            s.damping = damp.ctypes.data_as(dbl)
-            s.n_grid = int(p.n_grid)
-            s.trunc_L = float(p.trunc_L)
-            s.max_rank = int(p.max_rank)
-            s.seed = int(p.seed) & ((1 << 64) - 1)
-        self.count = len(problems)
+        n = len(problems)
+        self.count = n
+        self.rec = np.zeros(max(1, n), dtype=PROBLEM_DTYPE)
+        if n == 0:
+            self.arr = self.rec.ctypes.data_as(ctypes.POINTER(tt_problem))
+            return
+        d = np.fromiter((len(p.spot) for p in problems), dtype=np.int64, count=n)
+        self.spot = np.concatenate([np.asarray(p.spot, dtype=np.float64).ravel() for p in problems])
+        self.cov = np.concatenate([np.asarray(p.cov, dtype=np.float64).ravel() for p in problems])
+        self.damp = np.concatenate([np.asarray(p.damping, dtype=np.float64).ravel() for p in problems])
+        off1 = np.concatenate([[0], np.cumsum(d)[:-1]])
+        off2 = np.concatenate([[0], np.cumsum(d * d)[:-1]])
+        r = self.rec
+        r["d"] = d
+        r["spot"] = self.spot.ctypes.data + 8 * off1
+        r["cov"] = self.cov.ctypes.data + 8 * off2
+        r["damping"] = self.damp.ctypes.data + 8 * off1
+        r["rate"] = [float(p.rate) for p in problems]
+        r["maturity"] = [float(p.maturity) for p in problems]
+        r["strike"] = [float(p.strike) for p in problems]
+        r["payoff"] = [TT_MIN_CALL if p.payoff == "min" else TT_MAX_CALL for p in problems]
+        r["n_grid"] = [int(p.n_grid) for p in problems]
+        r["trunc_L"] = [float(p.trunc_L) for p in problems]
+        r["max_rank"] = [int(p.max_rank) for p in problems]
+        r["seed"] = [int(p.seed) & ((1 << 64) - 1) for p in problems]
+        self.arr = r.ctypes.data_as(ctypes.POINTER(tt_problem))
 
 
 class Pricer:

@@ -86,3 +86,27 @@ def test_struct_layouts_match_c():
     ]
     for line, w in zip(out, want):
         assert [int(v) for v in line.split()] == w
+
+
+def test_numpy_problem_record_matches_ctypes():
+    T = ttprice
+    assert T.PROBLEM_DTYPE.itemsize == ctypes.sizeof(T.tt_problem)
+    for name, _ in T.tt_problem._fields_:
+        assert T.PROBLEM_DTYPE.fields[name][1] == getattr(T.tt_problem, name).offset, name
+
+
+def test_problem_batch_packs_pointers():
+    import numpy as np
+
+    from paper_2203_02804_gb300 import inputs
+
+    ps = [inputs.two_asset_min_call(), inputs.five_asset_batch(1)[0], inputs.two_asset_min_call(payoff="max")]
+    b = ttprice.ProblemBatch(ps)
+    for i, p in enumerate(ps):
+        rec = b.arr[i]
+        assert rec.d == p.d and rec.n_grid == p.n_grid and rec.max_rank == p.max_rank
+        assert [rec.spot[j] for j in range(p.d)] == list(np.asarray(p.spot, dtype=float))
+        assert [rec.cov[j] for j in range(p.d * p.d)] == list(np.asarray(p.cov, dtype=float).ravel())
+        assert [rec.damping[j] for j in range(p.d)] == list(np.asarray(p.damping, dtype=float))
+        assert rec.payoff == (ttprice.TT_MIN_CALL if p.payoff == "min" else ttprice.TT_MAX_CALL)
+        assert rec.seed == p.seed

@@ -1,0 +1,74 @@
+"""The heterogeneous batch at full size: 4096 problems of uneven d, N and rank,
+calls on the minimum and on the maximum mixed 50/50, in one launch.
+
+The whole batch runs in the launch configuration the library uses for any batch;
+sampled problems are checked against the FP64 oracle one by one (the mixed path
+to 1e-4, the FP64 path to 1e-6), and every price is checked for the properties
+that hold at any size: a finite positive price, a status that is OK or
+not-converged, and an imaginary part of the grid sum that is small next to the
+price (the midpoint grid is symmetric, so the exact grid sum is real)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ttcross
+from paper_2203_02804_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_02804_gb300 import build, ttprice
+
+    build.build()
+    return ttprice
+
+
+def _cost(p):
+    return p.d * p.n_grid * p.max_rank ** 2 * (p.d if p.payoff == "max" else 1)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return inputs.mixed_batch(4096)
+
+
+def _run(tp, problems, precision):
+    pr = tp.Pricer(max_d=10, max_n=256, max_rank=32, max_batch=len(problems), precision=precision)
+    rc, prices, diags = pr.evaluate(problems)
+    pr.close()
+    return rc, prices, diags
+
+
+def test_full_heterogeneous_batch_mixed(tp, batch):
+    rc, prices, diags = _run(tp, batch, "mixed")
+    status = np.array([d.status for d in diags])
+    assert np.all((status == tp.TT_OK) | (status == tp.TT_WARN_NOT_CONVERGED))
+    assert np.all(np.isfinite(prices)) and np.all(prices > 0)
+    imag = np.array([d.imag_part for d in diags])
+    assert np.all(np.abs(imag) <= 1e-3 * np.abs(prices) + 1e-9)
+    assert sum(d.terms for d in diags) == sum(p.d if p.payoff == "max" else 1 for p in batch)
+    # sampled parity: the cheapest rank-32 problems of each payoff (rank 32 makes
+    # the train's own error small, so FP32 pivot choices that part from FP64 at
+    # near-ties stay inside 1e-4), priced one by one by the oracle
+    for payoff in ("min", "max"):
+        idx = sorted((i for i, p in enumerate(batch) if p.payoff == payoff and p.max_rank == 32),
+                     key=lambda i: _cost(batch[i]))[:3]
+        for i in idx:
+            ref, _, _ = ttcross.tt_price(batch[i])
+            assert abs(prices[i] / ref - 1) < 1e-4, (payoff, i)
+
+
+def test_heterogeneous_subset_fp64(tp, batch):
+    idx = sorted(range(len(batch)), key=lambda i: _cost(batch[i]))[:8]
+    sub = [batch[i] for i in idx]
+    rc, prices, diags = _run(tp, sub, "fp64")
+    for p, v, dg in zip(sub, prices, diags):
+        assert dg.status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
+        ref, _, _ = ttcross.tt_price(p)
+        assert math.isfinite(v) and abs(v / ref - 1) < 1e-6
