@@ -105,7 +105,8 @@ typedef struct {
   int fail_step;         /* for TT_ERR_NUMERIC: 1 fiber of rank 0, 2 singular pivot
                             block in maxvol, 3 singular interpolation solve,
                             4 non-finite estimate; 5 initial pivots not drawable   */
-  int reserved;
+  int maxvol_rollbacks;  /* cores whose maxvol returned to its last verified pivot set
+                            after the working-precision pivot block became singular */
   double imag_part;      /* Im of the discrete sum; 0 up to the TT error           */
   double flops;          /* arithmetic of the elimination, maxvol, interpolation
                             and integrand steps, by formula (see DESIGN notes)     */

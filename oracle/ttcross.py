@@ -19,7 +19,11 @@ What the paper fixes (Section IV.A-B) and what is read into it
         screened in blocks of 512 rows, each 64-row sub-block offering its 16
         rows with the largest entries.  A column whose best pivot is at most
         ``theta`` times that column's largest entry is skipped (numerically
-        dependent); the kept columns set the rank;
+        dependent); the pivot block of the winners then drops the columns
+        whose block entries are at most theta times their largest fiber entry,
+        and is reduced by complete pivoting on its column-equilibrated entries
+        (stop at theta), which keeps its condition number near 1/theta; the
+        kept columns set the rank;
       - maxvol: B = A_c A_c[W]^{-1} on the kept columns, blocks visited
         cyclically; inside a block, while max |B_ij| > 1 + tau swap row i into
         slot j (rank-one update of B, at most rank-many swaps per block); stop
@@ -193,24 +197,68 @@ def screen_rows(a_mat, start, stop):
     return kept
 
 
-def tournament_select(a_mat, block_rows, theta):
+def tournament_select(a_mat, block_rows, theta, screen_mat=None):
     """Flat GEPP tournament; returns (winner rows, kept columns).
 
     Each merge runs GEPP on the current winners stacked on top of new
     candidates: the next block of ``block_rows`` rows when the fiber has at most
-    SCREEN_MIN_ROWS rows, else the screened rows of the next SCREEN_BLOCK rows.
+    SCREEN_MIN_ROWS rows, else the screened rows of the next SCREEN_BLOCK rows
+    (screening keys from ``screen_mat``, default ``a_mat``).
     """
     m = a_mat.shape[0]
+    keys_from = a_mat if screen_mat is None else screen_mat
     winners, cols = [], []
     step = block_rows if m <= SCREEN_MIN_ROWS else SCREEN_BLOCK
     for start in range(0, m, step):
         stop = min(m, start + step)
-        fresh = list(range(start, stop)) if m <= SCREEN_MIN_ROWS else screen_rows(a_mat, start, stop)
+        fresh = list(range(start, stop)) if m <= SCREEN_MIN_ROWS else screen_rows(keys_from, start, stop)
         cand = winners + fresh
         r, c = gepp_select(a_mat[cand, :], theta)
         winners = [cand[p] for p in r]
         cols = c
     return winners, cols
+
+
+def rank_reveal(p_mat, theta, col_ref=None):
+    """Rank-revealing reduction of the pivot block; returns (rows, cols) in pivot order.
+
+    1. A column whose largest |entry|^2 in the block is at most theta^2 times
+       ``col_ref`` (its largest |entry|^2 over the whole fiber column) is
+       numerically absent from the block and is dropped.
+    2. Gaussian elimination with complete pivoting on the column-equilibrated
+       block: every entry's |.|^2 is divided by its column's largest in the
+       block, at every step the largest such value of the remaining block
+       (first in row-major order on ties) is the pivot, and the reduction stops
+       when it is at most theta^2.
+    Both rules are invariant under column scaling, as the interpolation is; the
+    kept sub-block has condition number about 1/theta after column
+    equilibration, which the tournament's partial pivoting alone does not
+    guarantee."""
+    s = np.array(p_mat, dtype=np.complex128, copy=True)
+    q, n = s.shape
+    blockmax = (s.real ** 2 + s.imag ** 2).max(axis=0)
+    keep = blockmax > 0
+    if col_ref is not None:
+        keep &= blockmax > theta * theta * np.asarray(col_ref, dtype=np.float64)
+    scale = np.where(keep, blockmax, np.inf)  # a dropped column never pivots
+    free_r = np.ones(q, dtype=bool)
+    free_c = np.ones(n, dtype=bool)
+    rows, cols = [], []
+    while free_r.any() and free_c.any():
+        mag = (s.real ** 2 + s.imag ** 2) / scale[None, :]
+        mag[~free_r, :] = -1.0
+        mag[:, ~free_c] = -1.0
+        p, c = divmod(int(np.argmax(mag)), n)
+        if not (mag[p, c] > theta * theta):
+            break
+        rows.append(p)
+        cols.append(c)
+        free_r[p] = False
+        free_c[c] = False
+        mult = s[:, c] / s[p, c]
+        mult[~free_r] = 0.0
+        s -= np.outer(mult, s[p, :])
+    return rows, cols
 
 
 def maxvol_refine(a_cols, rows, block_rows, tau):
@@ -275,13 +323,29 @@ def _fiber(tensor, d, n, k, outer, cols, direction):
     return tensor(idx).reshape(no * n, nc)
 
 
+def column_scaled(a_mat):
+    """Each column times a power of two that brings its largest |entry| into
+    (1/2, 1]; all-zero columns unchanged.  Pivot choices, maxvol's B and the
+    interpolation core are invariant under column scaling; the scaling keeps
+    |a|^2 and the pivot-block inverse inside the FP64 range for fibers through
+    far tails.  No pivot decision depends on it: GEPP, maxvol and
+    ``rank_reveal`` are invariant under column scaling."""
+    cm = np.abs(a_mat).max(axis=0)
+    expo = np.where(cm > 0, np.ceil(np.log2(np.where(cm > 0, cm, 1.0))), 0.0)
+    return a_mat * np.exp2(-expo)
+
+
 def core_select(tensor, d, n, k, outer, cols, direction, opts, diag):
     """Select rows of core k's fiber; returns (new index set, summed interpolant)."""
-    a_mat = _fiber(tensor, d, n, k, outer, cols, direction)
-    diag.evaluations += a_mat.size
-    rows, keep = tournament_select(a_mat, opts.block_rows, opts.theta)
+    raw = _fiber(tensor, d, n, k, outer, cols, direction)
+    diag.evaluations += raw.size
+    a_mat = column_scaled(raw)
+    rows, keep = tournament_select(a_mat, opts.block_rows, opts.theta, screen_mat=raw)
     if not rows:
         raise FloatingPointError("fiber matrix has numerical rank 0")
+    col_ref = (a_mat.real ** 2 + a_mat.imag ** 2).max(axis=0)[keep]
+    pr, pc = rank_reveal(a_mat[rows][:, keep], opts.theta, col_ref)
+    rows, keep = [rows[i] for i in pr], [keep[j] for j in pc]
     a_cols = a_mat[:, keep]
     rows, swaps, ok = maxvol_refine(a_cols, rows, opts.block_rows, opts.tau)
     diag.swaps += swaps

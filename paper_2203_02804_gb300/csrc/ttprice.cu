@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
   }
   x.colmax = reinterpret_cast<R*>(smem + sl.colmax);
   x.cshift = reinterpret_cast<R*>(smem + sl.cshift);
+  x.cref = reinterpret_cast<R*>(smem + sl.cref);
   x.wrow = reinterpret_cast<int*>(smem + sl.wrow);
   x.wnew = reinterpret_cast<int*>(smem + sl.wnew);
   x.jp = reinterpret_cast<int*>(smem + sl.jp);
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       x.evals = 0;
       x.swaps = 0;
       x.visits = 0;
+      x.rollbacks = 0;
       x.fail_step = 0;
       x.misc[MISC_FAIL] = 0;
       x.misc[MISC_DRAW] = 0;
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       r.evaluations = x.evals;
       r.swaps = x.swaps;
       r.visits = x.visits;
+      r.rollbacks = x.rollbacks;
       r.status = status;
       r.half_sweeps = hs;
       r.max_rank = maxrank;
@@ -202,7 +205,7 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
   r.swaps = 0;
   r.visits = 0;
   r.fail_step = 0;
-  r.pad = 0;
+  r.rollbacks = 0;
   r.half_sweeps = 0;
   r.max_rank = 0;
   r.terms = count[i];
@@ -219,6 +222,7 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
     r.evaluations += q.evaluations;
     r.swaps += q.swaps;
     r.visits += q.visits;
+    r.rollbacks += q.rollbacks;
     if (q.fail_step != 0 && r.fail_step == 0) r.fail_step = q.fail_step;
     r.half_sweeps = max(r.half_sweeps, q.half_sweeps);
     r.max_rank = max(r.max_rank, q.max_rank);
@@ -308,7 +312,7 @@ Layout make_layout(const tt_options& o, bool f64) {
   L.lvec = take(r * d * 8);
   L.rvec = take(r * d * 8);
   L.pair = take(8 * r * r * rs);
-  L.P = take(r * r * 2 * rs);
+  L.P = take(2 * r * r * 2 * rs);  // P and the copy maxvol falls back to
   L.sacc = take(r * r * 16);
   L.chain = take(2 * r * 16);
   L.stride = align_up(off, A);
@@ -338,6 +342,7 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   S.tab = take(4 * n * rs);
   S.colmax = take(r * rs);
   S.cshift = take((r + 1) * rs);
+  S.cref = take((r + 1) * rs);
   S.wrow = take(r * 4);
   S.wnew = take(r * 4);
   S.jp = take(r * 4);
@@ -690,7 +695,7 @@ int results_impl(tt_pricer* h, double* prices, tt_diag* diag) {
       diag[i].maxvol_swaps = r.swaps;
       diag[i].block_visits = r.visits;
       diag[i].fail_step = r.fail_step;
-      diag[i].reserved = 0;
+      diag[i].maxvol_rollbacks = r.rollbacks;
       diag[i].imag_part = r.imag;
       diag[i].flops = r.flops;
     }

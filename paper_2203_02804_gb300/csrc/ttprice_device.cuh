@@ -7,7 +7,7 @@
 
 namespace ttp {
 
-enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3 };
+enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3, MISC_SING = 4 };
 enum : int { DIR_LR = 0, DIR_RL = 1 };
 
 // block sum of a complex double held by every thread; result valid in all threads
@@ -57,15 +57,37 @@ __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, doubl
     const int j = idx / n, i = idx % n;
     const double u = -jd.L + (i + 0.5) * eta;
     const double dl = delta[j];
-    double lr = -0.5 * log(u * u + dl * dl);
-    double ph = -pcoef[j] * u - atan2(u, -dl);
-    if (kind[j] != 0.0) {
-      const double e = 1.0 - dl;
-      lr += -0.5 * log(u * u + e * e);
-      ph -= atan2(u, e);
+    double lr, c, s;
+    if constexpr (sizeof(R) == 4) {
+      // Mixed path: the linear phase p_j u (tens of radians) is formed and reduced
+      // modulo 2 pi in FP64; the bounded parts (log-magnitudes, the arguments of
+      // the rational factors, the sine/cosine of the reduced angle) in FP32.
+      const float uf = (float)u, df = (float)dl;
+      float lrf = -0.5f * logf(uf * uf + df * df);
+      float pr = -atan2f(uf, -df);
+      if (kind[j] != 0.0) {
+        const float ef = 1.0f - df;
+        lrf += -0.5f * logf(uf * uf + ef * ef);
+        pr -= atan2f(uf, ef);
+      }
+      const double lin = -pcoef[j] * u;
+      const double turns = rint(lin * 0.15915494309189535);  // 1/(2 pi)
+      const float red = (float)fma(-turns, 6.283185307179586, lin) + pr;
+      float sf, cf;
+      sincosf(red, &sf, &cf);
+      lr = lrf;
+      c = cf;
+      s = sf;
+    } else {
+      lr = -0.5 * log(u * u + dl * dl);
+      double ph = -pcoef[j] * u - atan2(u, -dl);
+      if (kind[j] != 0.0) {
+        const double e = 1.0 - dl;
+        lr += -0.5 * log(u * u + e * e);
+        ph -= atan2(u, e);
+      }
+      sincos(ph, &s, &c);
     }
-    double s, c;
-    sincos(ph, &s, &c);
     x.lam[(size_t)j * x.nmax + i] = lr;
     x.om[(size_t)j * x.nmax + i] = make_double2(c, s);
   }
@@ -267,11 +289,13 @@ __device__ void load_axis_table(Ctx<R>& x, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 only: shift every fiber column by a power of two so that its largest
-// entry has magnitude about one.  Elimination pivots and maxvol's B = A P^{-1}
-// are invariant under column scaling, and the contraction step v S P^{-1}
-// sees the same scale in S and P, so the shift changes no result; it keeps
-// |a|^2 and reciprocals inside the FP32 range for columns through far tails.
+// Shift every fiber column by a power of two so that its largest entry has
+// magnitude in (1/2, 1], and record that largest |entry|^2 (shifted units) for
+// the rank reveal.  Elimination pivots and maxvol's B = A P^{-1} are invariant
+// under column scaling, and the contraction step v S P^{-1} sees the same
+// scale in S and P, so the shift changes no exact result; it keeps |a|^2 and
+// the pivot-block inverse inside the floating-point range for columns through
+// far tails.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ void column_shifts(Ctx<R>& x, int no, int nc) {
@@ -282,7 +306,11 @@ __device__ void column_shifts(Ctx<R>& x, int no, int nc) {
       for (int r = lane; r < m; r += 32) mx = fmax(mx, eval_logmag(x, r / N, r % N, c));
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      if (lane == 0) x.cshift[c] = ceilf(mx);
+      if (lane == 0) {
+        const R sh = Num<R>::ceil_(mx);
+        x.cshift[c] = sh;
+        x.cref[c] = Num<R>::ex(R(2) * (mx - sh));
+      }
     }
     if (threadIdx.x == 0) x.flops += 4.0 * (double)m * nc;
     __syncthreads();
@@ -362,10 +390,11 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
 }
 
 // ---------------------------------------------------------------------------
-// M = P^{-1} by Gauss-Jordan with partial pivoting, in R, scratch in sw
+// M = P^{-1} by Gauss-Jordan with partial pivoting, in R, scratch in sw.
+// Returns false (M not written) when a pivot is zero or not finite.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ void invert_pivots(Ctx<R>& x, int rho) {
+__device__ bool invert_pivots(Ctx<R>& x, int rho) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int w2 = 2 * rho, ld = w2 + 1;  // odd row stride: column accesses are conflict-free
   cpx<R>* G = x.sw;
@@ -374,6 +403,7 @@ __device__ void invert_pivots(Ctx<R>& x, int rho) {
     G[r * ld + c] = x.P[r * x.rall + c];
     G[r * ld + rho + c] = cpx<R>{R(r == c), R(0)};
   }
+  if (tid == 0) x.misc[MISC_SING] = 0;
   __syncthreads();
   for (int c = 0; c < rho; ++c) {
     if (warp == 0) {
@@ -383,13 +413,11 @@ __device__ void invert_pivots(Ctx<R>& x, int rho) {
       warp_argmax(v, vi);
       if (lane == 0) {
         x.misc[MISC_PIV] = vi;
-        if (!(v > R(0))) {
-          x.misc[MISC_FAIL] = 1;
-          x.fail_step = 2;
-        }
+        if (!(v > R(0)) || !(v < R(INFINITY))) x.misc[MISC_SING] = 1;
       }
     }
     __syncthreads();
+    if (x.misc[MISC_SING]) break;  // block-uniform
     const int p = x.misc[MISC_PIV];
     if (p != c && p < rho) {
       for (int j = tid; j < w2; j += kThreads) {
@@ -413,12 +441,16 @@ __device__ void invert_pivots(Ctx<R>& x, int rho) {
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < rho * rho; idx += kThreads) {
-    const int r = idx / rho, c = idx % rho;
-    x.M[r * x.rall + c] = G[r * ld + rho + c];
+  const bool ok = !x.misc[MISC_SING];
+  if (ok) {
+    for (int idx = tid; idx < rho * rho; idx += kThreads) {
+      const int r = idx / rho, c = idx % rho;
+      x.M[r * x.rall + c] = G[r * ld + rho + c];
+    }
   }
   if (tid == 0) x.flops += 8.0 * (double)rho * rho * (2.0 * rho);
   __syncthreads();
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -586,10 +618,101 @@ __device__ int tournament(Ctx<R>& x, int m, int nc, int b, R thr2) {
 }
 
 // ---------------------------------------------------------------------------
+// Rank-revealing reduction of the winners' pivot block A[W, Jp] (rho x rho):
+//  1. a column whose largest |entry|^2 in the block is at most theta^2 times
+//     its largest over the whole fiber is numerically absent and is dropped;
+//  2. complete pivoting on the column-equilibrated block: each entry's |.|^2
+//     over its column's largest in the block; the next pivot is the largest
+//     such value of the remaining block (lowest row-major index on ties), and
+//     the reduction stops once it is at most theta^2.
+// Both rules are invariant under column scaling.  The kept rows and columns,
+// in pivot order, form a block of condition number about 1/theta after column
+// equilibration (the tournament's partial pivoting alone leaves some far
+// worse).  W and Jp are reordered and P = A[W, Jp] is built; returns the rank.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ int rank_reveal(Ctx<R>& x, int rho, R thr2) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ld = rho + 1, tot = rho * rho;
+  cpx<R>* __restrict__ G = x.sw;  // odd row stride: row and column reads are conflict-free
+  for (int idx = tid; idx < tot; idx += kThreads) {
+    const int j = idx / rho, t = idx % rho;
+    G[j * ld + t] = x.wvals[x.jp[t] * x.rall + j];
+  }
+  __syncthreads();
+  R* cm = x.colmax;  // equilibration: the column's largest |entry|^2 in the block (inf: dropped)
+  for (int t = warp; t < rho; t += kWarps) {
+    R mx = 0;
+    for (int j = lane; j < rho; j += 32) mx = fmax(mx, cabs2(G[j * ld + t]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) cm[t] = (mx > R(0) && mx > thr2 * x.cref[x.jp[t]]) ? mx : R(INFINITY);
+  }
+  __syncthreads();
+  R v = R(-1);
+  int vi = INT_MAX;
+  for (int idx = tid; idx < tot; idx += kThreads) {
+    const int j = idx / rho, t = idx % rho;
+    am_merge(v, vi, cabs2(G[j * ld + t]) / cm[t], idx);
+  }
+  int buf = 0;
+  block_argmax(v, vi, x.redv, x.redi, buf);
+  unsigned long long free_r = ~0ull, free_c = ~0ull;  // rho <= 64
+  int k = 0;
+  long long fl = 0;
+  // v, vi and the masks are block-uniform: every thread runs the same steps
+  while (k < rho && v > thr2) {
+    const int p = vi / rho, c = vi % rho;
+    if (tid == 0) {
+      x.selr[k] = p;
+      x.selc[k] = c;
+    }
+    free_r &= ~(1ull << p);
+    free_c &= ~(1ull << c);
+    ++k;
+    fl += (long long)(rho - k) * (rho - k);
+    // eliminate with the pivot (row p and column c are only read in this step)
+    const cpx<R> ip = crecip(G[p * ld + c]);
+    v = R(-1);
+    vi = INT_MAX;
+    for (int idx = tid; idx < tot; idx += kThreads) {
+      const int r = idx / rho, j = idx % rho;
+      if ((free_r >> r & 1ull) && (free_c >> j & 1ull)) {
+        cpx<R> a = G[r * ld + j];
+        cfms(a, cmul(G[r * ld + c], ip), G[p * ld + j]);
+        G[r * ld + j] = a;
+        am_merge(v, vi, cabs2(a) / cm[j], idx);
+      }
+    }
+    buf ^= 1;
+    block_argmax(v, vi, x.redv, x.redi, buf);  // its barrier also publishes the updates
+  }
+  for (int idx = tid; idx < k * k; idx += kThreads) {
+    const int s = idx / k, t = idx % k;
+    x.P[s * x.rall + t] = x.wvals[x.jp[x.selc[t]] * x.rall + x.selr[s]];
+  }
+  for (int s = tid; s < k; s += kThreads) {
+    x.wnew[s] = x.wrow[x.selr[s]];
+    x.scand[s] = x.jp[x.selc[s]];
+  }
+  __syncthreads();
+  for (int s = tid; s < k; s += kThreads) {
+    x.wrow[s] = x.wnew[s];
+    x.jp[s] = x.scand[s];
+  }
+  if (tid == 0) x.flops += 8.0 * (double)fl + 4.0 * (double)tot;
+  __syncthreads();
+  return k;
+}
+
+// ---------------------------------------------------------------------------
 // cyclic block maxvol on the kept columns (rows W start from the tournament)
 // P holds A[W, Jp]; M = P^{-1} is kept current by rank-one (Sherman-Morrison)
 // updates at each swap and recomputed after kRefreshSwaps of them.
 // The first cycle also accumulates the row sums S[o, t] = sum_i A[(o,i), Jp[t]].
+// Every successful recomputation saves (W, P).  If a recomputation finds P
+// singular in working precision (swaps chosen from a drifted FP32 inverse),
+// W and P return to the saved pair and the core's maxvol ends there: no more
+// swaps, only the row sums of the blocks the first cycle has not reached.
 // ---------------------------------------------------------------------------
 constexpr int kRefreshSwaps = 16;
 
@@ -607,19 +730,47 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
   const int nct = (rho + 3) / 4;
   const int rtiles = kThreads / nct;  // row tiles per round: thread (rt, ct) owns rows rt + a*rtiles
   const int rpr = 4 * rtiles;
+  int ncs = 0;  // pair columns to stage: up to the largest kept column (Jp is in pivot order)
+  for (int t = 0; t < rho; ++t) ncs = max(ncs, x.jp[t] + 1);
+  cpx<R>* Psave = x.P + x.rall * x.rall;
+  bool saved = false, frozen = false;
   while (quiet < nb && visits < 4 * nb) {
-    if (since_inv >= kRefreshSwaps) {
+    if (since_inv >= kRefreshSwaps && !frozen) {
       TTP_TIC(t_inv);
-      invert_pivots(x, rho);
+      if (invert_pivots(x, rho)) {
+        for (int idx = tid; idx < rho * rho; idx += kThreads) {
+          const int j = idx / rho, t = idx % rho;
+          Psave[j * x.rall + t] = x.P[j * x.rall + t];
+        }
+        for (int t = tid; t < rho; t += kThreads) x.wnew[t] = x.wrow[t];
+        saved = true;
+      } else if (saved) {
+        for (int idx = tid; idx < rho * rho; idx += kThreads) {
+          const int j = idx / rho, t = idx % rho;
+          x.P[j * x.rall + t] = Psave[j * x.rall + t];
+        }
+        for (int t = tid; t < rho; t += kThreads) x.wrow[t] = x.wnew[t];
+        __syncthreads();
+        invert_pivots(x, rho);  // the saved P inverted before
+        frozen = true;
+        if (tid == 0) x.rollbacks += 1;
+      } else {
+        if (tid == 0) {
+          x.misc[MISC_FAIL] = 1;
+          x.fail_step = 2;
+        }
+        break;
+      }
       since_inv = 0;
+      __syncthreads();
       TTP_TOC(t_inv, 5);
     }
+    if (frozen && visits >= nb) break;
     TTP_TIC(t_rev);
     const int rs = beta * b;
     const int bs = min(b, m - rs);
     cpx<R>* A = x.sw;  // bs x rho, column-major, leading dimension b
-    // stage_pairs needs the kept columns' entries: stage all columns up to the largest kept one
-    stage_pairs(x, rs / N, (rs + bs - 1) / N, x.jp[rho - 1] + 1);
+    stage_pairs(x, rs / N, (rs + bs - 1) / N, ncs);
     // rows of this block that are pivots already: their B rows are unit vectors,
     // never maxvol candidates (excluding them only guards against FP32 drift)
     unsigned char* inw = reinterpret_cast<unsigned char*>(x.scand);
@@ -631,7 +782,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       const int o = g / N;
       for (int t = tid >> 7; t < rho; t += 2) A[t * b + rr] = eval_row_point(x, rt, o, x.jp[t]);
     }
-    if (tid == 0) x.flops += 24.0 * bs * rho + 8.0 * (double)bs * rho * rho;
+    if (tid == 0) x.flops += 24.0 * bs * rho + (frozen ? 0.0 : 8.0 * (double)bs * rho * rho);
     __syncthreads();
     TTP_TOC(t_rev, 6);
     TTP_TIC(t_gemm);
@@ -672,7 +823,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
     // B = A M in row strips; each strip is read completely before it is overwritten
     R bv = R(-1);
     int bi = INT_MAX;
-    for (int r0 = 0; r0 < bs; r0 += rpr) {
+    for (int r0 = 0; r0 < (frozen ? 0 : bs); r0 += rpr) {
       const int rt = tid % rtiles, ct = tid / rtiles;
       const int col0 = 4 * ct;
       const bool act = ct < nct && r0 + rt < bs;
@@ -712,8 +863,10 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
           }
       }
     }
-    buf ^= 1;
-    block_argmax(bv, bi, x.redv, x.redi, buf);
+    if (!frozen) {  // block-uniform
+      buf ^= 1;
+      block_argmax(bv, bi, x.redv, x.redi, buf);
+    }
     TTP_TOC(t_gemm, 8);
     TTP_TIC(t_sw);
     bool swapped = false;
@@ -892,8 +1045,9 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
   TTP_TIC(t_cs);
   column_shifts(x, no, nc);
   TTP_TOC(t_cs, 1);
-  const int rho = tournament(x, m, nc, b, (R)(kn.theta * kn.theta));
-  if (rho == 0) {
+  const R thr2 = (R)(kn.theta * kn.theta);
+  const int rho0 = tournament(x, m, nc, b, thr2);
+  if (rho0 == 0) {
     if (tid == 0) {
       x.misc[MISC_FAIL] = 1;
       x.fail_step = 1;
@@ -901,12 +1055,9 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
     __syncthreads();
     return 0;
   }
-  // P = A[W, Jp] from the cached winner rows
-  for (int idx = tid; idx < rho * rho; idx += kThreads) {
-    const int j = idx / rho, t = idx % rho;
-    x.P[j * x.rall + t] = x.wvals[x.jp[t] * x.rall + j];
-  }
-  __syncthreads();
+  TTP_TIC(t_rr);
+  const int rho = rank_reveal(x, rho0, thr2);
+  TTP_TOC(t_rr, 7);
   maxvol_refine(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));
   TTP_TIC(t_ch);
   chain_solve(x, no, rho);
@@ -960,7 +1111,7 @@ __device__ double2 core_sum(Ctx<R>& x, int k, int dir, double* dscr) {
     x.flops += 24.0 * (double)no * N;
   }
   if constexpr (Num<R>::kScaleColumns) {
-    const double sc = exp2((double)x.cshift[0]);
+    const double sc = Num<R>::unscale((double)x.cshift[0]);
     est.x *= sc;
     est.y *= sc;
   }

@@ -71,7 +71,7 @@ __device__ __forceinline__ void cfms(cpx<R>& acc, cpx<R> a, cpx<R> b) {  // acc 
 }
 template <typename R>
 __device__ __forceinline__ R cabs2(cpx<R> a) {
-  return a.re * a.re + a.im * a.im;
+  return fma(a.re, a.re, a.im * a.im);  // one fixed rounding sequence at every call site
 }
 // 1/a by Smith's method (Smith 1962): no squares of the operands, so it stays
 // finite for any nonzero a in range.  FP32 uses the fast reciprocal (its error
@@ -96,17 +96,29 @@ __device__ __forceinline__ cpx<R> crecip(cpx<R> a) {
 
 // exp of the log-magnitude: FP32 tables hold E in log2 units, FP64 in natural units.
 template <typename R> struct Num;
+// Both paths scale every fiber column so that its largest entry is about one
+// (kScaleColumns): fibers through far tails reach magnitudes whose squares and
+// whose pivot-block inverses leave the floating-point range (~1e-20 in FP32,
+// ~1e-200 in FP64 for the call on the maximum).  `unscale` undoes a shift.
 template <> struct Num<float> {
   static constexpr double kLogScale = 1.4426950408889634;  // log2(e)
-  static constexpr bool kScaleColumns = true;  // FP32 range needs per-column power-of-two scaling
+  static constexpr bool kScaleColumns = true;  // power-of-two shifts
   __device__ static __forceinline__ float ex(float e) { return exp2f(e); }
   __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  __device__ static __forceinline__ double unscale(double shift) { return exp2(shift); }
+  __device__ static __forceinline__ float ceil_(float v) { return ceilf(v); }
+  __device__ static __forceinline__ float logu(float v) { return __log2f(v); }
 };
 template <> struct Num<double> {
   static constexpr double kLogScale = 1.0;
-  static constexpr bool kScaleColumns = false;
+  static constexpr bool kScaleColumns = true;  // power-of-two shifts, as k ln 2
   __device__ static __forceinline__ double ex(double e) { return exp(e); }
   __device__ static __forceinline__ double div(double a, double b) { return a / b; }
+  __device__ static __forceinline__ double unscale(double shift) { return exp(shift); }
+  __device__ static __forceinline__ double ceil_(double v) {
+    return ceil(v * 1.4426950408889634) * 0.6931471805599453;
+  }
+  __device__ static __forceinline__ double logu(double v) { return log(v); }
 };
 
 // ---------------------------------------------------------------------------
@@ -128,13 +140,13 @@ struct JobResult {
   double norm_sum;        // sum over axes of the per-axis log normalisation
   double flops;
   long long evaluations, swaps, visits;
-  int status, half_sweeps, max_rank, fail_step;
+  int status, half_sweeps, max_rank, fail_step, rollbacks;
 };
 
 struct InstanceResult {
   double price, imag, flops;
   long long evaluations, swaps, visits;
-  int status, half_sweeps, max_rank, terms, fail_step, pad;
+  int status, half_sweeps, max_rank, terms, fail_step, rollbacks;
 };
 
 struct Knobs {
@@ -153,7 +165,7 @@ struct Layout {
 
 // shared-memory carve, byte offsets (sizes depend on R)
 struct SmemLayout {
-  int sw, m, wvals, stage, tab, colmax, cshift, wrow, wnew, jp, selr, selc, scand, scnt, redv, redi, redk, swcol,
+  int sw, m, wvals, stage, tab, colmax, cshift, cref, wrow, wnew, jp, selr, selc, scand, scnt, redv, redi, redk, swcol,
       swrow, mcol, lsz, rsz, misc, total;
   int sw_elems;
 };
@@ -265,7 +277,7 @@ struct Ctx {
   double* lvec;       // [rmax_all][dmax]
   double* rvec;
   PairE<R>* pair;     // [rmax_all][rmax_all]
-  cpx<R>* P;          // [rmax_all][rmax_all] pivot rows A[W, Jp]
+  cpx<R>* P;          // [rmax_all][rmax_all] pivot rows A[W, Jp], then the saved copy
   double2* sacc;      // [rmax_all][rmax_all]
   double2* vchain;    // [rmax_all]
   double2* ychain;    // [rmax_all]
@@ -281,7 +293,8 @@ struct Ctx {
   R* tor;
   R* toi;
   R* colmax;
-  R* cshift;  // per-column exponent shift (log2 units, integer valued), FP32 only
+  R* cshift;  // per-column shift of the log-magnitude (a power of two of the value)
+  R* cref;    // per-column largest |entry|^2 over the fiber, shifted units (in (1/4, 1])
   int* wrow;
   int* wnew;
   int* jp;
@@ -301,6 +314,7 @@ struct Ctx {
   // bookkeeping (thread 0 only)
   double flops;
   long long evals, swaps, visits;
+  int rollbacks;
   int fail_step;
 };
 
@@ -322,11 +336,19 @@ __device__ __forceinline__ const PairE<R>& pair_at(const Ctx<R>& x, int o, int c
   return x.pair[o * x.rall + col];
 }
 
-// log-magnitude (scaled units) of the integrand at one fiber point, before shifts
+// log-magnitude (scaled units) of the integrand at one fiber point, before
+// shifts; the phase factors have unit modulus, the min-call's Cauchy factor
+// 1/(D0 + i s) has modulus (s^2 + D0^2)^(-1/2)
 template <typename R>
 __device__ __forceinline__ R eval_logmag(const Ctx<R>& x, int o, int i, int col) {
   const PairE<R>& q = pair_at(x, o, col);
-  return q.e0 + x.tl[i] + q.h * x.tu[i];
+  const R ui = x.tu[i];
+  R e = q.e0 + x.tl[i] + q.h * ui;
+  if (x.cauchy) {
+    const R s = q.s0 + ui;
+    e -= R(0.5) * Num<R>::logu(fma(s, s, x.D0 * x.D0));
+  }
+  return e;
 }
 
 // ---------------------------------------------------------------------------

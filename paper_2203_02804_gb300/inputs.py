@@ -85,9 +85,16 @@ def mixed_batch(count, index=2, d_range=(3, 10), grids=(64, 128, 256), ranks=(8,
     """Heterogeneous batch: d~U{3..10}, N~U{64,128,256}, rank~U{8,16,32},
     K~U[80,120], T~U[0.25,2], sigma_j~U[0.1,0.4], rho~U[0,0.6] (equicorrelated),
     payoff min/max with probability 1/2, S0_j=100, r=0.02, alpha=-1.5.
-    Truncation L = 8 / min_j(s_j sqrt T) over the per-axis spreads s_j that the
-    payoff's integrand sees (sigma_j for the min-call; for the max-call also
-    the spread volatilities sqrt(sigma_j^2 + sigma_l^2 - 2 rho sigma_j sigma_l))."""
+
+    Truncation L balances the two errors of the midpoint rule for the drawn N:
+    the cut tail, about exp(-s^2 T L^2 / 2) for the slowest-decaying axis (s the
+    smallest per-axis spread the payoff's integrand sees: sigma_j for the
+    min-call, for the max-call also the spread volatilities
+    sqrt(sigma_j^2 + sigma_l^2 - 2 rho sigma_j sigma_l)), and the aliasing of
+    the log-price function at period 2 pi / eta = pi N / L, about
+    exp(-(1/2) pi N / L) for damping 1.5 (the damped payoff decays as e^{-x/2}).
+    Equal exponents give L = (pi N / (s^2 T))^(1/3).  A fixed L = 8/(s sqrt T)
+    would leave eta = 2L/N too coarse for N = 64 on slow axes."""
     rng = np.random.default_rng(SEED_BASE + index)
     out = []
     for n in range(count):
@@ -105,7 +112,8 @@ def mixed_batch(count, index=2, d_range=(3, 10), grids=(64, 128, 256), ranks=(8,
                                         - 2.0 * rho * np.outer(sigma, sigma), 0.0))
             spread[np.eye(d, dtype=bool)] = np.inf
             vol = np.minimum(vol, spread.min(axis=1))
-        trunc = 8.0 / float(vol.min() * np.sqrt(maturity))
+        s2t = float(vol.min()) ** 2 * maturity
+        trunc = float(np.cbrt(np.pi * n_grid / s2t))
         out.append(Problem(spot=np.full(d, 100.0), cov=cov_from(sigma, equicorrelation(d, rho)),
                            rate=0.02, maturity=maturity, strike=strike, payoff=payoff,
                            damping=np.full(d, -1.5), n_grid=n_grid, trunc_L=trunc,

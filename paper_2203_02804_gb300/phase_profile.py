@@ -22,7 +22,7 @@ from . import build, inputs, ttprice
 
 PHASES = ["pair table + axis table", "column shifts", "tournament: evaluation + screening",
           "tournament: GEPP", "tournament: winner rows", "maxvol: P^-1 refresh",
-          "maxvol: block evaluation", "-", "maxvol: row sums + block product + argmax",
+          "maxvol: block evaluation", "rank reveal (complete pivoting)", "maxvol: row sums + block product + argmax",
           "maxvol: swaps", "interpolation solve (FP64)", "-", "end-core sums",
           "job set-up (tables, pivots)"]
 

@@ -64,7 +64,7 @@ class tt_diag(ctypes.Structure):
                 ("final_rank_max", ctypes.c_int), ("terms", ctypes.c_int),
                 ("evaluations", ctypes.c_longlong), ("maxvol_swaps", ctypes.c_longlong),
                 ("block_visits", ctypes.c_longlong), ("fail_step", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("imag_part", ctypes.c_double),
+                ("maxvol_rollbacks", ctypes.c_int), ("imag_part", ctypes.c_double),
                 ("flops", ctypes.c_double)]
 
 
@@ -124,7 +124,7 @@ class Diag:
     maxvol_swaps: int
     block_visits: int
     fail_step: int
-    reserved: int
+    maxvol_rollbacks: int
     imag_part: float
     flops: float
 

@@ -109,11 +109,57 @@ def test_rank_two_additive_tensor_is_reproduced_exactly():
 
 
 def test_full_rank_cross_reproduces_full_grid_sum():
+    """Rank 16 on a 16 x 16 grid: the cross keeps every direction above the rank
+    threshold (1e-8 of the first pivot), so the train is the grid sum to ~1e-10."""
     p = inputs.two_asset_min_call(n_grid=16, max_rank=16)
     t = integrand.tensors_for(p)[0]
     est, dg = ttcross.tt_cross_sum(t, 16, seed=1)
     exact = integrand.full_grid_sum(t)
-    assert abs(est - exact) < 1e-11 * abs(exact)
+    assert abs(est - exact) < 1e-9 * abs(exact)
+
+
+def test_rank_reveal_keeps_a_well_conditioned_block():
+    """Complete pivoting on a block whose last columns are nearly dependent:
+    it stops at the numerical rank, and the kept sub-block has condition ~1/theta."""
+    rng = np.random.default_rng(31)
+    base = rng.standard_normal((8, 5)) + 1j * rng.standard_normal((8, 5))
+    mix = rng.standard_normal((5, 8))
+    block = base @ mix + 1e-12 * rng.standard_normal((8, 8))  # rank 5 up to 1e-12
+    rows, cols = ttcross.rank_reveal(block, 1e-8)
+    assert len(rows) == len(cols) == 5
+    assert np.linalg.cond(block[np.ix_(rows, cols)]) < 1e8
+    full_rows, _ = ttcross.rank_reveal(rng.standard_normal((6, 6)), 1e-8)
+    assert len(full_rows) == 6
+
+
+def test_rank_reveal_is_invariant_under_column_scaling():
+    """Columns scaled by 1e-150 .. 1e+150 (with their reference sizes): the same
+    pivots as unscaled, and a rank-1 block keeps one pivot."""
+    rng = np.random.default_rng(32)
+    block = rng.standard_normal((7, 7)) + 1j * rng.standard_normal((7, 7))
+    scale = 10.0 ** rng.uniform(-150, 150, 7)
+    ref = rng.uniform(1.0, 3.0, 7) * (np.abs(block) ** 2).max(axis=0)
+    assert ttcross.rank_reveal(block, 1e-8) == ttcross.rank_reveal(block * scale, 1e-8)
+    assert ttcross.rank_reveal(block, 1e-8, ref) == ttcross.rank_reveal(block * scale, 1e-8, ref * scale ** 2)
+    # equilibrated: every column's largest entry scores exactly 1, so the first
+    # pivot is the one of them that comes first in row-major order
+    rows, cols = ttcross.rank_reveal(block * scale, 1e-8)
+    col_argmax = np.abs(block).argmax(axis=0)
+    assert (rows[0], cols[0]) == min((int(col_argmax[c]), c) for c in range(7))
+    x = rng.standard_normal(7) + 1j * rng.standard_normal(7)
+    rows, cols = ttcross.rank_reveal(np.outer(x, x * scale), 1e-8)
+    assert len(rows) == 1 and rows[0] == int(np.argmax(np.abs(x)))
+
+
+def test_rank_reveal_drops_a_column_negligible_in_its_fiber():
+    """A column whose block entries are 1e-10 of its fiber-wide size is numerically
+    absent from the block (below theta = 1e-8 once measured against its fiber)."""
+    rng = np.random.default_rng(33)
+    block = rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5))
+    ref = (np.abs(block) ** 2).max(axis=0)
+    ref[2] *= 1e20
+    rows, cols = ttcross.rank_reveal(block, 1e-8, ref)
+    assert len(cols) == 4 and 2 not in cols
 
 
 def test_single_axis_sum_is_plain_sum():
