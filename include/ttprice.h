@@ -68,7 +68,9 @@ typedef struct {
                            largest entry is dropped (numerically dependent)        */
   double maxvol_tol;    /* <= 0 -> 0.05: maxvol stops when all |B_ij| <= 1 + tol  */
   int block_rows;       /* 0 -> 128: rows per elimination/maxvol block;
-                           needs max_rank <= block_rows <= 256 - max_rank          */
+                           needs max_rank <= block_rows <= 256 - max_rank, and
+                           block_rows <= 128 for TT_MIXED (the maxvol
+                           block product is one 128-row tensor-core tile)        */
   int device;           /* CUDA device ordinal                                     */
   void* cuda_stream;    /* cudaStream_t to run on; NULL = legacy default stream    */
   void* workspace;      /* optional device buffer of tt_workspace_bytes() bytes,
@@ -104,7 +106,8 @@ typedef struct {
   long long block_visits; /* maxvol block visits (one block product B = A P^{-1} each) */
   int fail_step;         /* for TT_ERR_NUMERIC: 1 fiber of rank 0, 2 singular pivot
                             block in maxvol, 3 singular interpolation solve,
-                            4 non-finite estimate; 5 initial pivots not drawable   */
+                            4 non-finite estimate; 5 initial pivots not drawable;
+                            6 a tensor-core block product did not complete (mixed) */
   int maxvol_rollbacks;  /* cores whose maxvol returned to its last verified pivot set
                             after the working-precision pivot block became singular */
   double imag_part;      /* Im of the discrete sum; 0 up to the TT error           */

@@ -92,8 +92,24 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
   x.lsz = reinterpret_cast<int*>(smem + sl.lsz);
   x.rsz = reinterpret_cast<int*>(smem + sl.rsz);
   x.misc = reinterpret_cast<int*>(smem + sl.misc);
+  x.mbar = reinterpret_cast<uint64_t*>(x.misc + MISC_MBAR);
+  x.tmem_cols = tc::tmem_cols(lay.rmax);
+  x.mma_phase = 0;
+  x.tc_pending = 0;
   }
   __syncthreads();
+  if constexpr (kTensorCoreMaxvol<R>) {
+    if (tid == 0) {
+      tc::mbar_init(x.mbar);
+      tc::mbar_init(x.mbar + 1);
+    }
+    if (tid < 32) tc::tmem_alloc(reinterpret_cast<uint32_t*>(x.misc + MISC_TMEM), x.tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) x.tmem = *reinterpret_cast<uint32_t*>(x.misc + MISC_TMEM);
+    __syncthreads();
+  }
 
   for (int guard = 0; guard < njobs + 1; ++guard) {  // at most njobs jobs per CTA
     if (tid == 0) x.misc[MISC_JOB] = atomicAdd(counter, 1);
@@ -189,6 +205,18 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
     }
     __syncthreads();
   }
+  if constexpr (kTensorCoreMaxvol<R>) {
+    // a block product whose completion wait gave up may still be running: wait
+    // (bounded) before the accumulator columns are released
+    if (x.tc_pending) {
+      tc::mbar_wait(x.mbar, x.mma_phase & 1u);
+      tc::mbar_wait(x.mbar + 1, (x.mma_phase >> 1) & 1u);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid < 32) tc::tmem_dealloc(x.tmem, x.tmem_cols);
+  }
 }
 
 // per-instance combination of the trains: price = sum Re(weight sign e^{logscale+norms} est)
@@ -271,6 +299,8 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.precision != TT_FP64 && o.precision != TT_MIXED) return false;
   if (o.block_rows == 0) o.block_rows = 128;
   if (o.block_rows < o.max_rank || o.block_rows + o.max_rank > ttp::kThreads) return false;
+  // the mixed path's maxvol block product is one 128-row tensor-core tile
+  if (o.precision == TT_MIXED && o.block_rows > ttp::tc::kRows) return false;
   if (o.max_half_sweeps == 0) o.max_half_sweeps = 8;
   if (o.max_half_sweeps < 1 || o.max_half_sweeps > 1000) return false;
   const bool f64 = o.precision == TT_FP64;
@@ -328,6 +358,9 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   const int r = o.max_rank, b = o.block_rows, n = o.max_n, d = o.max_d;
   int sw_elems = std::max((r + std::max(b, 128)) * r, 2 * r * r);
   sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + cs - 1) / cs);
+  const int kp = ttp::tc::pad16(r);
+  // FP32: two buffers of four 128-row planes of one 8-column chunk (hi and lo parts of Re A and Im A)
+  if (!f64) sw_elems = std::max(sw_elems, 2 * 4 * ttp::tc::kRows * ttp::kTcChunk * 4 / cs);
   int off = 0;
   auto take = [&](int bytes) {
     int at = off;
@@ -336,8 +369,8 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   };
   S.sw_elems = sw_elems;
   S.sw = take(sw_elems * cs);
-  S.m = take(r * r * cs);
-  S.wvals = take(r * r * cs);
+  S.m = take(f64 ? r * r * cs : 2 * kp * kp * 4);  // FP32: hi planes (re, im) of P^{-1}
+  S.wvals = take(f64 ? r * r * cs : std::max(r * r * cs, 2 * kp * kp * 4));  // FP32: also the lo planes
   S.stage = take(ttp::kStageO * r * 8 * rs);
   S.tab = take(4 * n * rs);
   S.colmax = take(r * rs);
@@ -427,6 +460,25 @@ int grid_for(const tt_options& o, const SmemLayout& S, int* grid_out) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TT_ERR_CUDA;
+  }
+  if (o.precision != TT_FP64) {
+    // The occupancy query answers 1 block per SM for this kernel once it holds
+    // tensor memory, although 3 x 64 of the SM's 512 TMEM columns are free for
+    // it; residency here is set by registers and shared memory, counted directly.
+    // (A CTA that finds no free slot starts when one ends and finds the job
+    // queue empty, so an over-count costs nothing.)
+    cudaFuncAttributes fa;
+    int smem_sm = 0, regs_sm = 0;
+    if (cudaFuncGetAttributes(&fa, ttp::tt_cross_kernel<float>) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, o.device) == cudaSuccess &&
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, o.device) == cudaSuccess) {
+      const int by_smem = smem_sm / (S.total + (int)fa.sharedSizeBytes + 1024);
+      const int by_regs = regs_sm / std::max(1, fa.numRegs * ttp::kThreads);
+      const int by_tmem = 512 / (int)ttp::tc::tmem_cols(o.max_rank);
+      per_sm = std::max(per_sm, std::min(std::min(by_smem, by_regs), by_tmem));
+    } else {
+      cudaGetLastError();
+    }
   }
   if (per_sm < 1) return TT_ERR_CAPACITY;
   *grid_out = dev_sms * per_sm;

@@ -4,10 +4,16 @@
 #include <climits>
 
 #include "ttprice_kernels.cuh"
+#include "ttprice_tc.cuh"
 
 namespace ttp {
 
-enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3, MISC_SING = 4 };
+enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3, MISC_SING = 4, MISC_MBAR = 8,
+             MISC_TMEM = 12 };  // MISC_MBAR: two 8-byte barriers (ints 8..11)
+
+// The FP32 path runs the maxvol block product on the tensor cores; FP64 on CUDA cores.
+template <typename R>
+constexpr bool kTensorCoreMaxvol = sizeof(R) == 4;
 enum : int { DIR_LR = 0, DIR_RL = 1 };
 
 // block sum of a complex double held by every thread; result valid in all threads
@@ -390,6 +396,39 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
 }
 
 // ---------------------------------------------------------------------------
+// P^{-1} of the FP32 path: hi and lo TF32 parts in K-major tensor-core planes
+// (hi in M, lo in the winner-value buffer, free during maxvol)
+// ---------------------------------------------------------------------------
+constexpr int kTcChunk = 8;  // kept columns per evaluation/MMA chunk (one K step), two buffers
+
+__device__ __forceinline__ float tf32_hi(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// P^{-1}[t][s] from / to its hi and lo planes (row s, k t of the B operand)
+template <typename R>
+__device__ __forceinline__ cpx<R> minv_get(const Ctx<R>& x, int kp, int t, int s) {
+  const int sbo = kp * 32, off = tc::kmaj(s, t, sbo), plane = (kp / 8) * sbo;
+  const unsigned char* hi = reinterpret_cast<const unsigned char*>(x.M);
+  const unsigned char* lo = reinterpret_cast<const unsigned char*>(x.wvals);
+  return {*reinterpret_cast<const R*>(hi + off) + *reinterpret_cast<const R*>(lo + off),
+          *reinterpret_cast<const R*>(hi + plane + off) + *reinterpret_cast<const R*>(lo + plane + off)};
+}
+template <typename R>
+__device__ __forceinline__ void minv_set(Ctx<R>& x, int kp, int t, int s, cpx<R> v) {
+  const int sbo = kp * 32, off = tc::kmaj(s, t, sbo), plane = (kp / 8) * sbo;
+  unsigned char* hi = reinterpret_cast<unsigned char*>(x.M);
+  unsigned char* lo = reinterpret_cast<unsigned char*>(x.wvals);
+  const R hr = tf32_hi(v.re), hm = tf32_hi(v.im);
+  *reinterpret_cast<R*>(hi + off) = hr;
+  *reinterpret_cast<R*>(lo + off) = v.re - hr;
+  *reinterpret_cast<R*>(hi + plane + off) = hm;
+  *reinterpret_cast<R*>(lo + plane + off) = v.im - hm;
+}
+
+// ---------------------------------------------------------------------------
 // M = P^{-1} by Gauss-Jordan with partial pivoting, in R, scratch in sw.
 // Returns false (M not written) when a pivot is zero or not finite.
 // ---------------------------------------------------------------------------
@@ -443,9 +482,18 @@ __device__ bool invert_pivots(Ctx<R>& x, int rho) {
   }
   const bool ok = !x.misc[MISC_SING];
   if (ok) {
-    for (int idx = tid; idx < rho * rho; idx += kThreads) {
-      const int r = idx / rho, c = idx % rho;
-      x.M[r * x.rall + c] = G[r * ld + rho + c];
+    if constexpr (kTensorCoreMaxvol<R>) {
+      // the tensor-core operand: hi and lo K-major planes, zero outside rho x rho
+      const int kp = tc::pad16(rho);
+      for (int idx = tid; idx < kp * kp; idx += kThreads) {
+        const int r = idx / kp, c = idx % kp;
+        minv_set(x, kp, r, c, (r < rho && c < rho) ? G[r * ld + rho + c] : cpx<R>{R(0), R(0)});
+      }
+    } else {
+      for (int idx = tid; idx < rho * rho; idx += kThreads) {
+        const int r = idx / rho, c = idx % rho;
+        x.M[r * x.rall + c] = G[r * ld + rho + c];
+      }
     }
   }
   if (tid == 0) x.flops += 8.0 * (double)rho * rho * (2.0 * rho);
@@ -924,6 +972,328 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32 maxvol with the block product on the tensor cores.  Same visits, swaps,
+// rollback and row sums as maxvol_refine.  Per visit the block's fiber rows at
+// the kept columns are evaluated in chunks of 8 columns into four K-major
+// planes (hi and lo TF32 parts of Re A and Im A, 128 rows zero-padded), double
+// buffered so that one chunk's products run while the next is evaluated, and
+// multiplied into TMEM with 3xTF32 products
+//   A P^{-1} ~ A_hi M_hi + A_hi M_lo + A_lo M_hi,
+// as two real products of N = 2 kp, D = Re A [Re M | Im M] and
+// E = Im A [Re M | Im M]; the read-back combines them, B = (D_re - E_im) +
+// i (D_im + E_re), and stores complex B[t*b + r] for the swaps.
+// P^{-1} is kept as its own hi and lo planes (M_hi in M, M_lo in the winner-
+// value buffer, free during maxvol); their sum is the FP32 inverse.  One TF32
+// product (2^-11) is not enough: B = A P^{-1} cancels by up to the condition
+// number of P (up to 1/theta), and 3xTF32 brings the rounding to ~2^-21.
+// The row of B that updates P^{-1} at a swap is recomputed in FP32 from the
+// evaluated pivot row.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
+  static_assert(sizeof(R) == 4, "the tensor-core maxvol is the FP32 path");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = x.n;
+  const int nb = (m + b - 1) / b;
+  const int kp = tc::pad16(rho);
+  // A chunk planes: 128 rows x 8 columns, 256 bytes per 8-row group, 4 KB each;
+  // a buffer holds four (hi and lo of Re A and Im A), two buffers
+  constexpr int kSboA = kTcChunk * 32, kPlaneA = (tc::kRows / 8) * kSboA, kBufA = 4 * kPlaneA;
+  unsigned char* a_pl = reinterpret_cast<unsigned char*>(x.sw);
+  const int sbo_m = kp * 32;
+  // P^{-1} operands (hi in M, lo in wvals): the re plane, then the im plane
+  const unsigned char* m_hi = reinterpret_cast<const unsigned char*>(x.M);
+  const unsigned char* m_lo = reinterpret_cast<const unsigned char*>(x.wvals);
+  cpx<R>* B = x.sw;  // after the product: bs x rho, column-major, leading dimension b
+  for (int idx = tid; idx < no * rho; idx += kThreads) {
+    const int o = idx / rho, t = idx % rho;
+    x.sacc[o * x.rall + t] = make_double2(0.0, 0.0);
+  }
+  if (x.tc_pending) {  // an earlier product never completed: no more tensor-core work in this CTA
+    if (tid == 0) {
+      x.misc[MISC_FAIL] = 1;
+      x.fail_step = 6;
+    }
+    __syncthreads();
+    return;
+  }
+  uint32_t phase[2] = {x.mma_phase & 1u, (x.mma_phase >> 1) & 1u};  // per buffer barrier; block-uniform
+  int quiet = 0, visits = 0, beta = 0, since_inv = kRefreshSwaps;
+  int buf = 0;
+  long long nswaps = 0;
+  int ncs = 0;  // pair columns to stage: up to the largest kept column (Jp is in pivot order)
+  for (int t = 0; t < rho; ++t) ncs = max(ncs, x.jp[t] + 1);
+  cpx<R>* Psave = x.P + x.rall * x.rall;
+  bool saved = false, frozen = false;
+  while (quiet < nb && visits < 4 * nb) {
+    if (since_inv >= kRefreshSwaps && !frozen) {
+      TTP_TIC(t_inv);
+      if (invert_pivots(x, rho)) {
+        for (int idx = tid; idx < rho * rho; idx += kThreads) {
+          const int j = idx / rho, t = idx % rho;
+          Psave[j * x.rall + t] = x.P[j * x.rall + t];
+        }
+        for (int t = tid; t < rho; t += kThreads) x.wnew[t] = x.wrow[t];
+        saved = true;
+      } else if (saved) {
+        for (int idx = tid; idx < rho * rho; idx += kThreads) {
+          const int j = idx / rho, t = idx % rho;
+          x.P[j * x.rall + t] = Psave[j * x.rall + t];
+        }
+        for (int t = tid; t < rho; t += kThreads) x.wrow[t] = x.wnew[t];
+        __syncthreads();
+        invert_pivots(x, rho);  // the saved P inverted before
+        frozen = true;
+        if (tid == 0) x.rollbacks += 1;
+      } else {
+        if (tid == 0) {
+          x.misc[MISC_FAIL] = 1;
+          x.fail_step = 2;
+        }
+        break;
+      }
+      since_inv = 0;
+      __syncthreads();
+      TTP_TOC(t_inv, 5);
+    }
+    if (frozen && visits >= nb) break;
+    TTP_TIC(t_rev);
+    const int rs = beta * b;
+    const int bs = min(b, m - rs);
+    stage_pairs(x, rs / N, (rs + bs - 1) / N, ncs);
+    // rows of this block that are pivots already: their B rows are unit vectors,
+    // never maxvol candidates (excluding them guards against rounding)
+    unsigned char* inw = reinterpret_cast<unsigned char*>(x.scand);
+    for (int r = tid; r < bs; r += kThreads) inw[r] = 0;
+    __syncthreads();
+    for (int t = tid; t < rho; t += kThreads) {
+      const int g = x.wrow[t] - rs;
+      if (g >= 0 && g < bs) inw[g] = 1;
+    }
+    bool failed = false;
+    // chunk c of 8 kept columns goes to buffer c & 1; its 12 MMAs run while chunk
+    // c + 1 is evaluated into the other buffer.  Buffer k's products complete on
+    // barrier k, so each barrier has at most one phase outstanding.
+    const int nch = kp / kTcChunk;
+    for (int c = 0; c < nch && !failed; ++c) {
+      const int bufk = c & 1, c0 = c * kTcChunk;
+      unsigned char* const pb = a_pl + bufk * kBufA;
+      if (!frozen && c >= 2) {  // the products that last read this buffer
+        const bool ok = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+        phase[bufk] ^= 1u;
+      }
+      // evaluation: lane -> rows 8g + lane/4 (two row groups per warp), columns
+      // lane%4 and lane%4 + 4; a warp's store is 8 rows x 4 columns = 128 bytes
+      TTP_TIC(t_ev8);
+#pragma unroll
+      for (int gg = 0; gg < 2; ++gg) {
+        const int r = 8 * (2 * warp + gg) + (lane >> 2);
+        const bool live = r < bs;
+        const int g = rs + (live ? r : 0);
+        const RowTab<R> rt = row_tab(x, g % N);
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int tl = (lane & 3) + 4 * jj, t = c0 + tl;
+          cpx<R> v = {R(0), R(0)};
+          if (live && t < rho) v = eval_row_point(x, rt, g / N, x.jp[t]);
+          const int off = tc::kmaj(r, tl, kSboA);
+          const R hr = tf32_hi(v.re), hm = tf32_hi(v.im);
+          *reinterpret_cast<R*>(pb + off) = hr;
+          *reinterpret_cast<R*>(pb + kPlaneA + off) = hm;
+          *reinterpret_cast<R*>(pb + 2 * kPlaneA + off) = v.re - hr;
+          *reinterpret_cast<R*>(pb + 3 * kPlaneA + off) = v.im - hm;
+        }
+      }
+      TTP_TOC(t_ev8, 14);
+      tc::fence_async_smem();  // the planes (and P^{-1} after swaps) were written by the generic proxy
+      __syncthreads();
+      if (!frozen && tid == 0) {
+        TTP_TIC(t_mma);
+        tc::fence_after_sync();
+        // D = Re A [M_re | M_im] and E = Im A [M_re | M_im] (N = 2 kp: the re and im
+        // planes of P^{-1} are adjacent), each as hi*hi + hi*lo + lo*hi; a plane
+        // further on is (byte offset >> 4) further in the start-address field
+        const uint64_t a0 = tc::smem_desc(tc::smem_u32(pb), (uint32_t)kSboA), ap = kPlaneA >> 4;
+        const uint32_t km = (uint32_t)(c0 / 4) * 128u;
+        const uint64_t mh = tc::smem_desc(tc::smem_u32(m_hi) + km, (uint32_t)sbo_m);
+        const uint64_t ml = tc::smem_desc(tc::smem_u32(m_lo) + km, (uint32_t)sbo_m);
+        const uint32_t id = tc::instr_desc(2 * kp, false), te = x.tmem + (uint32_t)(2 * kp);
+        const uint32_t acc = c > 0 ? 1u : 0u;
+        tc::mma_tf32(x.tmem, a0, mh, id, acc);      // Re A hi * M hi
+        tc::mma_tf32(te, a0 + ap, mh, id, acc);     // Im A hi * M hi
+        tc::mma_tf32(x.tmem, a0, ml, id, 1u);       // Re A hi * M lo
+        tc::mma_tf32(te, a0 + ap, ml, id, 1u);      // Im A hi * M lo
+        tc::mma_tf32(x.tmem, a0 + 2 * ap, mh, id, 1u);  // Re A lo * M hi
+        tc::mma_tf32(te, a0 + 3 * ap, mh, id, 1u);      // Im A lo * M hi
+        tc::commit(x.mbar + bufk);
+        TTP_TOC(t_mma, 11);
+      }
+      TTP_TIC(t_rsum);
+      if (visits < nb) {  // first cycle: row sums of this chunk's columns (the MMAs only read)
+        // one warp per (outer index, kept column); lanes take rows, compensated
+        // (Kahan) partial sums, a fixed-order warp reduction, FP64 accumulator
+        const int olo = rs / N, ohi = (rs + bs - 1) / N;
+        const int nol = ohi - olo + 1, ncol = min(kTcChunk, rho - c0);
+        for (int pr = warp; pr < nol * ncol; pr += kWarps) {
+          const int ol = pr % nol, tl = pr / nol;
+          const int o = olo + ol;
+          const int r0 = max(o * N, rs) - rs, r1 = min(o * N + N, rs + bs) - rs;
+          R sr = 0, si = 0, cr = 0, ci = 0;
+          for (int r = r0 + lane; r < r1; r += 32) {
+            const int off = tc::kmaj(r, tl, kSboA);
+            const R are = *reinterpret_cast<const R*>(pb + off) + *reinterpret_cast<const R*>(pb + 2 * kPlaneA + off);
+            const R aim = *reinterpret_cast<const R*>(pb + kPlaneA + off) +
+                          *reinterpret_cast<const R*>(pb + 3 * kPlaneA + off);
+            R y = are - cr; R s2 = sr + y; cr = (s2 - sr) - y; sr = s2;
+            y = aim - ci; s2 = si + y; ci = (s2 - si) - y; si = s2;
+          }
+          R vr = sr - cr, vi = si - ci;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, off);
+            vi += __shfl_xor_sync(0xffffffffu, vi, off);
+          }
+          if (lane == 0) {
+            double2& acc = x.sacc[o * x.rall + c0 + tl];
+            acc.x += (double)vr;
+            acc.y += (double)vi;
+          }
+        }
+      }
+      TTP_TOC(t_rsum, 15);
+      if (frozen) __syncthreads();  // the next chunk overwrites what the row sums read
+    }
+    // the products of the last two chunks
+    if (!frozen && !failed) {
+      for (int c = max(0, nch - 2); c < nch; ++c) {
+        const int bufk = c & 1;
+        const bool ok = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+        phase[bufk] ^= 1u;
+      }
+    }
+    if (failed) {
+      if (tid == 0) {
+        x.misc[MISC_FAIL] = 1;
+        x.fail_step = 6;
+        x.tc_pending = 1;
+        x.mma_phase = phase[0] | (phase[1] << 1);  // the phases still outstanding
+      }
+      __syncthreads();
+      break;
+    }
+    if (tid == 0) x.flops += 24.0 * bs * rho + (frozen ? 0.0 : 24.0 * (double)bs * rho * rho);
+    TTP_TOC(t_rev, 6);
+    TTP_TIC(t_gemm);
+    R bv = R(-1);
+    int bi = INT_MAX;
+    if (!frozen) {
+      tc::fence_after_sync();
+      // warp quarter q reads TMEM lanes (block rows) 32q..32q+31; warp half h the
+      // columns [h kp/2, (h+1) kp/2) of both accumulators
+      const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
+      for (int cc = h * (kp / 2); cc < (h + 1) * (kp / 2); cc += 8) {
+        float dr[8], di[8], er[8], ei[8];
+        const uint32_t ta = x.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cc;
+        tc::tmem_ld8(ta, dr);
+        tc::tmem_ld8(ta + (uint32_t)kp, di);
+        tc::tmem_ld8(ta + (uint32_t)(2 * kp), er);
+        tc::tmem_ld8(ta + (uint32_t)(3 * kp), ei);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int s = cc + c;
+          if (row < bs && s < rho) {
+            const cpx<R> v = {dr[c] - ei[c], di[c] + er[c]};  // Re A M + i Im A M
+            B[s * b + row] = v;
+            if (!inw[row]) am_merge(bv, bi, cabs2(v), row * rho + s);
+          }
+        }
+      }
+      tc::fence_before_sync();
+      buf ^= 1;
+      block_argmax(bv, bi, x.redv, x.redi, buf);  // its barrier also publishes B
+    }
+    TTP_TOC(t_gemm, 8);
+    TTP_TIC(t_sw);
+    bool swapped = false;
+    for (int it = 0; it < rho; ++it) {
+      if (!(bv > thr)) break;
+      const int i = bi / rho, j = bi % rho;
+      for (int r = tid; r < bs; r += kThreads) x.swcol[r] = B[j * b + r];
+      for (int t = tid; t < rho; t += kThreads) x.mcol[t] = minv_get(x, kp, t, j);
+      if (tid == 0) {
+        const int old = x.wrow[j] - rs;
+        if (old >= 0 && old < bs) inw[old] = 0;
+        inw[i] = 1;
+        x.wrow[j] = rs + i;
+      }
+      __syncthreads();
+      eval_prow(x, j, rs + i, rho);  // P[j][t] = A(i, t), exact FP32
+      __syncthreads();
+      // the swapped-in row of B in FP32: B(i, s) = sum_t P[j][t] P^{-1}[t][s],
+      // eight lanes per output column
+      for (int s0 = 0; s0 < rho; s0 += 4 * kWarps) {
+        const int s = s0 + 4 * warp + (lane >> 3), sub = lane & 7;
+        cpx<R> acc = {R(0), R(0)};
+        if (s < rho)
+          for (int t = sub; t < rho; t += 8) cfma(acc, x.P[j * x.rall + t], minv_get(x, kp, t, s));
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+          acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
+          acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
+        }
+        if (s < rho && sub == 0) x.swrow[s] = acc;
+      }
+      __syncthreads();
+      const cpx<R> ipiv = crecip(x.swrow[j]);
+      bv = R(-1);
+      bi = INT_MAX;
+      for (int idx = tid; idx < bs * rho; idx += kThreads) {
+        const int r = idx % bs, t = idx / bs;
+        cpx<R> rv = x.swrow[t];
+        if (t == j) rv.re -= R(1);
+        cpx<R> bb = B[t * b + r];
+        cfms(bb, x.swcol[r], cmul(rv, ipiv));
+        B[t * b + r] = bb;
+        if (!inw[r]) am_merge(bv, bi, cabs2(bb), r * rho + t);
+      }
+      for (int idx = tid; idx < rho * rho; idx += kThreads) {
+        const int r = idx / rho, t = idx % rho;
+        cpx<R> rv = x.swrow[t];
+        if (t == j) rv.re -= R(1);
+        cpx<R> mv = minv_get(x, kp, r, t);
+        cfms(mv, x.mcol[r], cmul(rv, ipiv));
+        minv_set(x, kp, r, t, mv);
+      }
+      if (tid == 0) x.flops += 8.0 * (bs + 2 * rho) * rho + 24.0 * rho;
+      buf ^= 1;
+      block_argmax(bv, bi, x.redv, x.redi, buf);
+      swapped = true;
+      ++since_inv;
+      ++nswaps;
+    }
+    quiet = swapped ? 0 : quiet + 1;
+    ++visits;
+    beta = (beta + 1) % nb;
+    __syncthreads();
+    TTP_TOC(t_sw, 9);
+  }
+  if (tid == 0) {
+    x.swaps += nswaps;
+    x.visits += visits;
+    if (!x.tc_pending) x.mma_phase = phase[0] | (phase[1] << 1);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // contraction step: v <- (v S) P^{-1}, FP64 (Gaussian elimination on P^T)
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -1058,7 +1428,19 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
   TTP_TIC(t_rr);
   const int rho = rank_reveal(x, rho0, thr2);
   TTP_TOC(t_rr, 7);
-  maxvol_refine(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));
+  if (rho == 0) {  // every column negligible in its fiber
+    if (tid == 0) {
+      x.misc[MISC_FAIL] = 1;
+      x.fail_step = 1;
+    }
+    __syncthreads();
+    return 0;
+  }
+  if constexpr (kTensorCoreMaxvol<R>) {
+    maxvol_refine_tc(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));
+  } else {
+    maxvol_refine(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));
+  }
   TTP_TIC(t_ch);
   chain_solve(x, no, rho);
   TTP_TOC(t_ch, 10);

@@ -315,6 +315,10 @@ struct Ctx {
   double flops;
   long long evals, swaps, visits;
   int rollbacks;
+  // FP32 path: tensor-core block product (completion barrier, TMEM accumulators)
+  uint64_t* mbar;  // two completion barriers, one per operand buffer
+  uint32_t tmem, tmem_cols, mma_phase;  // mma_phase: bit k = next parity of barrier k
+  int tc_pending;  // a completion wait gave up: wait again before releasing TMEM
   int fail_step;
 };
 

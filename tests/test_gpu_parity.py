@@ -92,6 +92,17 @@ def test_ragged_blocks_with_small_block_rows(tp):
     assert abs(prices[0] / ref - 1) < FP64_TOL
 
 
+def test_mixed_ragged_blocks_and_small_ranks(tp):
+    """The tensor-core block product with a ragged 16-row tail (zero-padded to the
+    128-row tile) and ranks below 16 (K and N padded to 16): rank 12 over 37^3
+    and rank 8 over 50^3 in blocks of 64 rows, against the FP64 oracle."""
+    for p, b in [(small_problem(3, 37, 12, seed=0), 128), (small_problem(3, 50, 8), 64)]:
+        rc, prices, diags = gpu_price(tp, [p], precision="mixed", block_rows=b)
+        assert diags[0].status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
+        ref = ttcross.tt_price(p, ttcross.CrossOptions(block_rows=b, theta=1e-5, sweep_tol=1e-4))[0]
+        assert abs(prices[0] / ref - 1) < 5e-3, (p.n_grid, b)
+
+
 def test_single_asset_is_the_grid_sum_and_black_scholes(tp):
     p = inputs.Problem(spot=np.array([105.0]), cov=np.array([[0.0625]]), rate=0.03, maturity=0.8,
                        strike=100.0, payoff="min", damping=np.array([-3.0]), n_grid=512,
