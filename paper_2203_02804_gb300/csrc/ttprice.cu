@@ -99,9 +99,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
   }
   __syncthreads();
   if constexpr (kTensorCoreMaxvol<R>) {
-    if (tid == 0) {
-      tc::mbar_init(x.mbar);
-      tc::mbar_init(x.mbar + 1);
+    if (tid == 0) {  // two arrivals per phase: the two issuing threads' commits
+      tc::mbar_init(x.mbar, 2);
+      tc::mbar_init(x.mbar + 1, 2);
     }
     if (tid < 32) tc::tmem_alloc(reinterpret_cast<uint32_t*>(x.misc + MISC_TMEM), x.tmem_cols);
     tc::fence_before_sync();

@@ -1077,13 +1077,10 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
     for (int c = 0; c < nch && !failed; ++c) {
       const int bufk = c & 1, c0 = c * kTcChunk;
       unsigned char* const pb = a_pl + bufk * kBufA;
-      if (!frozen && c >= 2) {  // the products that last read this buffer
-        const bool ok = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
-        if (__syncthreads_or(!ok)) {
-          failed = true;
-          break;
-        }
-        phase[bufk] ^= 1u;
+      bool ok = true;
+      if (!frozen && c >= 2) {  // the products that last read this buffer (checked at the next barrier)
+        ok = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
+        if (ok) phase[bufk] ^= 1u;  // a phase that timed out stays the outstanding one
       }
       // evaluation: lane -> rows 8g + lane/4 (two row groups per warp), columns
       // lane%4 and lane%4 + 4; a warp's store is 8 rows x 4 columns = 128 bytes
@@ -1109,8 +1106,13 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       }
       TTP_TOC(t_ev8, 14);
       tc::fence_async_smem();  // the planes (and P^{-1} after swaps) were written by the generic proxy
-      __syncthreads();
-      if (!frozen && tid == 0) {
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      // two issuing threads in different warps, one per accumulator chain (the MMA
+      // queue is short, so one thread issuing all six would stall its warp)
+      if (!frozen && (tid & 127) == 0) {
         TTP_TIC(t_mma);
         tc::fence_after_sync();
         // D = Re A [M_re | M_im] and E = Im A [M_re | M_im] (N = 2 kp: the re and im
@@ -1120,15 +1122,16 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
         const uint32_t km = (uint32_t)(c0 / 4) * 128u;
         const uint64_t mh = tc::smem_desc(tc::smem_u32(m_hi) + km, (uint32_t)sbo_m);
         const uint64_t ml = tc::smem_desc(tc::smem_u32(m_lo) + km, (uint32_t)sbo_m);
-        const uint32_t id = tc::instr_desc(2 * kp, false), te = x.tmem + (uint32_t)(2 * kp);
+        const uint32_t id = tc::instr_desc(2 * kp, false);
         const uint32_t acc = c > 0 ? 1u : 0u;
-        tc::mma_tf32(x.tmem, a0, mh, id, acc);      // Re A hi * M hi
-        tc::mma_tf32(te, a0 + ap, mh, id, acc);     // Im A hi * M hi
-        tc::mma_tf32(x.tmem, a0, ml, id, 1u);       // Re A hi * M lo
-        tc::mma_tf32(te, a0 + ap, ml, id, 1u);      // Im A hi * M lo
-        tc::mma_tf32(x.tmem, a0 + 2 * ap, mh, id, 1u);  // Re A lo * M hi
-        tc::mma_tf32(te, a0 + 3 * ap, mh, id, 1u);      // Im A lo * M hi
-        tc::commit(x.mbar + bufk);
+        // thread 0: D = Re A [M] into columns [0, 2kp); thread 128: E = Im A [M] into [2kp, 4kp)
+        const int part = tid >> 7;
+        const uint32_t dst = x.tmem + (uint32_t)(part * 2 * kp);
+        const uint64_t ahi = a0 + (uint64_t)part * ap, alo = a0 + (uint64_t)(2 + part) * ap;
+        tc::mma_tf32(dst, ahi, mh, id, acc);  // A hi * M hi
+        tc::mma_tf32(dst, ahi, ml, id, 1u);   // A hi * M lo
+        tc::mma_tf32(dst, alo, mh, id, 1u);   // A lo * M hi
+        tc::commit(x.mbar + bufk);            // the barrier expects both issuing threads
         TTP_TOC(t_mma, 11);
       }
       TTP_TIC(t_rsum);
@@ -1168,15 +1171,14 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
     }
     // the products of the last two chunks
     if (!frozen && !failed) {
+      bool ok = true;
       for (int c = max(0, nch - 2); c < nch; ++c) {
         const int bufk = c & 1;
-        const bool ok = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
-        if (__syncthreads_or(!ok)) {
-          failed = true;
-          break;
-        }
-        phase[bufk] ^= 1u;
+        const bool done = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
+        if (done) phase[bufk] ^= 1u;
+        ok = ok && done;
       }
+      failed = __syncthreads_or(!ok);
     }
     if (failed) {
       if (tid == 0) {

@@ -60,8 +60,8 @@ __device__ __forceinline__ void commit(uint64_t* mbar) {
       smem_u32(mbar)));
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t arrivals) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(arrivals));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
