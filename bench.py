@@ -35,6 +35,35 @@ N_SM = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5, derived
+# DRAM traffic of the kernel from one ncu capture (profiles/), valid for the
+# kernel sources it was taken on
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tt_cross_kernel_float_d5_min_call.traffic.json")
+
+
+def kernel_source_digest():
+    """SHA-256 over the CUDA sources (the traffic record names the digest it was taken on)."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2203_02804_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(batch, precision):
+    """DRAM bytes per launch scaled from the ncu capture by problems priced, or None when
+    the capture is absent, of another precision, or of other kernel sources."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("precision") != precision or rec.get("source_sha256") != kernel_source_digest():
+        return None
+    return rec["dram_bytes_per_price"] * batch
 
 
 def workload_problems(batch, rank_offset=0):
@@ -262,7 +291,7 @@ def run_gpu(args):
                          "peak": FP32_PEAK_TFLOPS if args.precision == "mixed" else 1.26,
                          "unit": "TFLOP/s",
                          "frac": achieved / (FP32_PEAK_TFLOPS if args.precision == "mixed" else 1.26),
-                         "traffic": None,
+                         "traffic": traffic_per_launch(args.batch, args.precision),
                          "kernel": f"tt_cross_kernel<{'float' if args.precision == 'mixed' else 'double'}>",
                          "flops_per_launch": flops_per_step,
                          "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},

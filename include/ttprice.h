@@ -53,6 +53,11 @@ typedef enum { TT_MIN_CALL = 0, TT_MAX_CALL = 1 } tt_payoff;
  * and exponent arguments, the interpolation solve and the contraction in FP64. */
 typedef enum { TT_FP64 = 0, TT_MIXED = 1 } tt_precision;
 
+/* Engine of the maxvol block product in the mixed path (Section IV.B cross step):
+   FP32 FMA on the CUDA cores, or 3xTF32 tcgen05 MMAs with TMEM accumulators.
+   Results agree to the mixed path's tolerance; speed depends on the rank. */
+typedef enum { TT_ENGINE_AUTO = 0, TT_ENGINE_CUDA_CORES = 1, TT_ENGINE_TENSOR_CORES = 2 } tt_engine;
+
 typedef struct {
   int max_d;            /* largest number of assets                        (1..255)  */
   int max_n;            /* largest grid size N per axis                    (2..4096) */
@@ -69,8 +74,11 @@ typedef struct {
   double maxvol_tol;    /* <= 0 -> 0.05: maxvol stops when all |B_ij| <= 1 + tol  */
   int block_rows;       /* 0 -> 128: rows per elimination/maxvol block;
                            needs max_rank <= block_rows <= 256 - max_rank, and
-                           block_rows <= 128 for TT_MIXED (the maxvol
+                           block_rows <= 128 with TT_ENGINE_TENSOR_CORES (the
                            block product is one 128-row tensor-core tile)        */
+  int engine;           /* tt_engine of the maxvol block product B = A P^{-1};
+                           TT_ENGINE_AUTO picks CUDA cores up to max_rank 32 and
+                           tensor cores above; TT_FP64 always uses CUDA cores    */
   int device;           /* CUDA device ordinal                                     */
   void* cuda_stream;    /* cudaStream_t to run on; NULL = legacy default stream    */
   void* workspace;      /* optional device buffer of tt_workspace_bytes() bytes,

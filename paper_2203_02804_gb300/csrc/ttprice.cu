@@ -28,7 +28,7 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? TTP_MIN_BLOCKS_F32 : 1;  // FP32: several CTAs per SM
 };
 
-template <typename R>
+template <typename R, bool TC>
 __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel(const JobDesc* __restrict__ jobs,
                                                             const double* __restrict__ params,
                                                             const int* __restrict__ order, int njobs,
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
   x.tc_pending = 0;
   }
   __syncthreads();
-  if constexpr (kTensorCoreMaxvol<R>) {
+  if constexpr (TC) {
     if (tid == 0) {  // two arrivals per phase: the two issuing threads' commits
       tc::mbar_init(x.mbar, 2);
       tc::mbar_init(x.mbar + 1, 2);
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       __syncthreads();
       if ((s & 1) == 0) {
         for (int k = 0; k + 1 < d; ++k) {
-          const int rho = core_select(x, kn, k, DIR_LR);
+          const int rho = core_select<R, TC>(x, kn, k, DIR_LR);
           maxrank = max(maxrank, rho);
           if (x.misc[MISC_FAIL]) break;
         }
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
         TTP_TOC(t_cs, 12);
       } else {
         for (int k = d - 1; k >= 1; --k) {
-          const int rho = core_select(x, kn, k, DIR_RL);
+          const int rho = core_select<R, TC>(x, kn, k, DIR_RL);
           maxrank = max(maxrank, rho);
           if (x.misc[MISC_FAIL]) break;
         }
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
     }
     __syncthreads();
   }
-  if constexpr (kTensorCoreMaxvol<R>) {
+  if constexpr (TC) {
     // a block product whose completion wait gave up may still be running: wait
     // (bounded) before the accumulator columns are released
     if (x.tc_pending) {
@@ -299,8 +299,15 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.precision != TT_FP64 && o.precision != TT_MIXED) return false;
   if (o.block_rows == 0) o.block_rows = 128;
   if (o.block_rows < o.max_rank || o.block_rows + o.max_rank > ttp::kThreads) return false;
-  // the mixed path's maxvol block product is one 128-row tensor-core tile
-  if (o.precision == TT_MIXED && o.block_rows > ttp::tc::kRows) return false;
+  if (o.engine < TT_ENGINE_AUTO || o.engine > TT_ENGINE_TENSOR_CORES) return false;
+  if (o.precision == TT_FP64) {
+    if (o.engine == TT_ENGINE_TENSOR_CORES) return false;  // no FP64 tensor-core product
+    o.engine = TT_ENGINE_CUDA_CORES;
+  } else if (o.engine == TT_ENGINE_AUTO) {
+    o.engine = o.max_rank > 32 ? TT_ENGINE_TENSOR_CORES : TT_ENGINE_CUDA_CORES;
+  }
+  // the tensor-core block product is one 128-row tile
+  if (o.engine == TT_ENGINE_TENSOR_CORES && o.block_rows > ttp::tc::kRows) return false;
   if (o.max_half_sweeps == 0) o.max_half_sweeps = 8;
   if (o.max_half_sweeps < 1 || o.max_half_sweeps > 1000) return false;
   const bool f64 = o.precision == TT_FP64;
@@ -359,8 +366,10 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   int sw_elems = std::max((r + std::max(b, 128)) * r, 2 * r * r);
   sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + cs - 1) / cs);
   const int kp = ttp::tc::pad16(r);
-  // FP32: two buffers of four 128-row planes of one 8-column chunk (hi and lo parts of Re A and Im A)
-  if (!f64) sw_elems = std::max(sw_elems, 2 * 4 * ttp::tc::kRows * ttp::kTcChunk * 4 / cs);
+  const bool tcore = o.engine == TT_ENGINE_TENSOR_CORES;
+  // tensor cores: two buffers of four 128-row planes of one 8-column chunk (hi and lo
+  // parts of Re A and Im A)
+  if (tcore) sw_elems = std::max(sw_elems, 2 * 4 * ttp::tc::kRows * ttp::kTcChunk * 4 / cs);
   int off = 0;
   auto take = [&](int bytes) {
     int at = off;
@@ -369,8 +378,8 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   };
   S.sw_elems = sw_elems;
   S.sw = take(sw_elems * cs);
-  S.m = take(f64 ? r * r * cs : 2 * kp * kp * 4);  // FP32: hi planes (re, im) of P^{-1}
-  S.wvals = take(f64 ? r * r * cs : std::max(r * r * cs, 2 * kp * kp * 4));  // FP32: also the lo planes
+  S.m = take(tcore ? 2 * kp * kp * 4 : r * r * cs);  // tensor cores: hi planes (re, im) of P^{-1}
+  S.wvals = take(tcore ? std::max(r * r * cs, 2 * kp * kp * 4) : r * r * cs);  // tensor cores: also the lo planes
   S.stage = take(ttp::kStageO * r * 8 * rs);
   S.tab = take(4 * n * rs);
   S.colmax = take(r * rs);
@@ -432,45 +441,41 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   return D;
 }
 
+// shared-memory opt-in and blocks per SM for one instantiation of the kernel
+template <typename R, bool TC>
+cudaError_t kernel_occupancy(const SmemLayout& S, int* per_sm, cudaFuncAttributes* fa) {
+  cudaError_t e = cudaFuncSetAttribute(ttp::tt_cross_kernel<R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       S.total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ttp::tt_cross_kernel<R, TC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ttp::tt_cross_kernel<R, TC>, ttp::kThreads, S.total);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(fa, ttp::tt_cross_kernel<R, TC>);
+  return e;
+}
+
 int grid_for(const tt_options& o, const SmemLayout& S, int* grid_out) {
   int dev_sms = 0;
   if (cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess)
     return TT_ERR_CUDA;
   int per_sm = 0;
-  cudaError_t e;
-  if (o.precision == TT_FP64) {
-    e = cudaFuncSetAttribute(ttp::tt_cross_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             S.total);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ttp::tt_cross_kernel<double>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttp::tt_cross_kernel<double>,
-                                                        ttp::kThreads, S.total);
-  } else {
-    e = cudaFuncSetAttribute(ttp::tt_cross_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             S.total);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ttp::tt_cross_kernel<float>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttp::tt_cross_kernel<float>,
-                                                        ttp::kThreads, S.total);
-  }
+  cudaFuncAttributes fa;
+  const bool tcore = o.engine == TT_ENGINE_TENSOR_CORES;
+  cudaError_t e = o.precision == TT_FP64 ? kernel_occupancy<double, false>(S, &per_sm, &fa)
+                  : tcore                ? kernel_occupancy<float, true>(S, &per_sm, &fa)
+                                         : kernel_occupancy<float, false>(S, &per_sm, &fa);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TT_ERR_CUDA;
   }
-  if (o.precision != TT_FP64) {
+  if (tcore) {
     // The occupancy query answers 1 block per SM for this kernel once it holds
-    // tensor memory, although 3 x 64 of the SM's 512 TMEM columns are free for
-    // it; residency here is set by registers and shared memory, counted directly.
-    // (A CTA that finds no free slot starts when one ends and finds the job
-    // queue empty, so an over-count costs nothing.)
-    cudaFuncAttributes fa;
+    // tensor memory, although 3 x 128 of the SM's 512 TMEM columns are free for
+    // it; residency here is set by registers, shared memory and TMEM columns,
+    // counted directly.  (A CTA that finds no free slot starts when one ends and
+    // finds the job queue empty, so an over-count costs nothing.)
     int smem_sm = 0, regs_sm = 0;
-    if (cudaFuncGetAttributes(&fa, ttp::tt_cross_kernel<float>) == cudaSuccess &&
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, o.device) == cudaSuccess &&
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, o.device) == cudaSuccess &&
         cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, o.device) == cudaSuccess) {
       const int by_smem = smem_sm / (S.total + (int)fa.sharedSizeBytes + 1024);
       const int by_regs = regs_sm / std::max(1, fa.numRegs * ttp::kThreads);
@@ -710,10 +715,13 @@ int run_impl(tt_pricer* h) {
   if (h->njobs > 0) {
     const int grid = std::min(h->grid, h->njobs);
     if (h->R.o.precision == TT_FP64)
-      ttp::tt_cross_kernel<double><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+      ttp::tt_cross_kernel<double, false><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
+    else if (h->R.o.engine == TT_ENGINE_TENSOR_CORES)
+      ttp::tt_cross_kernel<float, true><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
           jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
     else
-      ttp::tt_cross_kernel<float><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+      ttp::tt_cross_kernel<float, false><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
           jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
     if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
   }

@@ -11,9 +11,8 @@ namespace ttp {
 enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3, MISC_SING = 4, MISC_MBAR = 8,
              MISC_TMEM = 12 };  // MISC_MBAR: two 8-byte barriers (ints 8..11)
 
-// The FP32 path runs the maxvol block product on the tensor cores; FP64 on CUDA cores.
-template <typename R>
-constexpr bool kTensorCoreMaxvol = sizeof(R) == 4;
+// Functions templated on <R, bool TC>: TC selects the maxvol block-product engine,
+// tensor cores (FP32 only: P^{-1} kept as hi/lo TF32 planes) or CUDA cores.
 enum : int { DIR_LR = 0, DIR_RL = 1 };
 
 // block sum of a complex double held by every thread; result valid in all threads
@@ -432,7 +431,7 @@ __device__ __forceinline__ void minv_set(Ctx<R>& x, int kp, int t, int s, cpx<R>
 // M = P^{-1} by Gauss-Jordan with partial pivoting, in R, scratch in sw.
 // Returns false (M not written) when a pivot is zero or not finite.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool TC>
 __device__ bool invert_pivots(Ctx<R>& x, int rho) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int w2 = 2 * rho, ld = w2 + 1;  // odd row stride: column accesses are conflict-free
@@ -482,7 +481,7 @@ __device__ bool invert_pivots(Ctx<R>& x, int rho) {
   }
   const bool ok = !x.misc[MISC_SING];
   if (ok) {
-    if constexpr (kTensorCoreMaxvol<R>) {
+    if constexpr (TC) {
       // the tensor-core operand: hi and lo K-major planes, zero outside rho x rho
       const int kp = tc::pad16(rho);
       for (int idx = tid; idx < kp * kp; idx += kThreads) {
@@ -785,7 +784,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
   while (quiet < nb && visits < 4 * nb) {
     if (since_inv >= kRefreshSwaps && !frozen) {
       TTP_TIC(t_inv);
-      if (invert_pivots(x, rho)) {
+      if (invert_pivots<R, false>(x, rho)) {
         for (int idx = tid; idx < rho * rho; idx += kThreads) {
           const int j = idx / rho, t = idx % rho;
           Psave[j * x.rall + t] = x.P[j * x.rall + t];
@@ -799,7 +798,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
         }
         for (int t = tid; t < rho; t += kThreads) x.wrow[t] = x.wnew[t];
         __syncthreads();
-        invert_pivots(x, rho);  // the saved P inverted before
+        invert_pivots<R, false>(x, rho);  // the saved P inverted before
         frozen = true;
         if (tid == 0) x.rollbacks += 1;
       } else {
@@ -985,9 +984,8 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
 // P^{-1} is kept as its own hi and lo planes (M_hi in M, M_lo in the winner-
 // value buffer, free during maxvol); their sum is the FP32 inverse.  One TF32
 // product (2^-11) is not enough: B = A P^{-1} cancels by up to the condition
-// number of P (up to 1/theta), and 3xTF32 brings the rounding to ~2^-21.
-// The row of B that updates P^{-1} at a swap is recomputed in FP32 from the
-// evaluated pivot row.
+// number of P (up to 1/theta), and 3xTF32 brings the rounding to ~2^-21, about
+// an FP32 product's, so the swapped-in row of B updates P^{-1} directly.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
@@ -1027,7 +1025,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
   while (quiet < nb && visits < 4 * nb) {
     if (since_inv >= kRefreshSwaps && !frozen) {
       TTP_TIC(t_inv);
-      if (invert_pivots(x, rho)) {
+      if (invert_pivots<R, true>(x, rho)) {
         for (int idx = tid; idx < rho * rho; idx += kThreads) {
           const int j = idx / rho, t = idx % rho;
           Psave[j * x.rall + t] = x.P[j * x.rall + t];
@@ -1041,7 +1039,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
         }
         for (int t = tid; t < rho; t += kThreads) x.wrow[t] = x.wnew[t];
         __syncthreads();
-        invert_pivots(x, rho);  // the saved P inverted before
+        invert_pivots<R, true>(x, rho);  // the saved P inverted before
         frozen = true;
         if (tid == 0) x.rollbacks += 1;
       } else {
@@ -1190,7 +1188,9 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       __syncthreads();
       break;
     }
-    if (tid == 0) x.flops += 24.0 * bs * rho + (frozen ? 0.0 : 24.0 * (double)bs * rho * rho);
+    // algorithmic work: 24 per evaluation, 8 per complex multiply-add of the block
+    // product (the 3xTF32 split triples the tensor-core work, not the algorithm's)
+    if (tid == 0) x.flops += 24.0 * bs * rho + (frozen ? 0.0 : 8.0 * (double)bs * rho * rho);
     TTP_TOC(t_rev, 6);
     TTP_TIC(t_gemm);
     R bv = R(-1);
@@ -1229,7 +1229,10 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       if (!(bv > thr)) break;
       const int i = bi / rho, j = bi % rho;
       for (int r = tid; r < bs; r += kThreads) x.swcol[r] = B[j * b + r];
-      for (int t = tid; t < rho; t += kThreads) x.mcol[t] = minv_get(x, kp, t, j);
+      for (int t = tid; t < rho; t += kThreads) {
+        x.swrow[t] = B[t * b + i];
+        x.mcol[t] = minv_get(x, kp, t, j);
+      }
       if (tid == 0) {
         const int old = x.wrow[j] - rs;
         if (old >= 0 && old < bs) inw[old] = 0;
@@ -1237,23 +1240,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
         x.wrow[j] = rs + i;
       }
       __syncthreads();
-      eval_prow(x, j, rs + i, rho);  // P[j][t] = A(i, t), exact FP32
-      __syncthreads();
-      // the swapped-in row of B in FP32: B(i, s) = sum_t P[j][t] P^{-1}[t][s],
-      // eight lanes per output column
-      for (int s0 = 0; s0 < rho; s0 += 4 * kWarps) {
-        const int s = s0 + 4 * warp + (lane >> 3), sub = lane & 7;
-        cpx<R> acc = {R(0), R(0)};
-        if (s < rho)
-          for (int t = sub; t < rho; t += 8) cfma(acc, x.P[j * x.rall + t], minv_get(x, kp, t, s));
-#pragma unroll
-        for (int off = 1; off < 8; off <<= 1) {
-          acc.re += __shfl_xor_sync(0xffffffffu, acc.re, off);
-          acc.im += __shfl_xor_sync(0xffffffffu, acc.im, off);
-        }
-        if (s < rho && sub == 0) x.swrow[s] = acc;
-      }
-      __syncthreads();
+      eval_prow(x, j, rs + i, rho);  // P[j][t] = A(i, t), FP32
       const cpx<R> ipiv = crecip(x.swrow[j]);
       bv = R(-1);
       bi = INT_MAX;
@@ -1401,7 +1388,7 @@ __device__ void chain_solve(Ctx<R>& x, int no, int rho) {
 // ---------------------------------------------------------------------------
 // one core of a half-sweep: tournament, maxvol, interpolation solve, new index set
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool TC>
 __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
   const int tid = threadIdx.x;
   const int N = x.n;
@@ -1438,7 +1425,7 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
     __syncthreads();
     return 0;
   }
-  if constexpr (kTensorCoreMaxvol<R>) {
+  if constexpr (TC) {
     maxvol_refine_tc(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));
   } else {
     maxvol_refine(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));

@@ -28,6 +28,10 @@ TT_MIN_CALL = 0
 TT_MAX_CALL = 1
 TT_FP64 = 0
 TT_MIXED = 1
+TT_ENGINE_AUTO = 0
+TT_ENGINE_CUDA_CORES = 1
+TT_ENGINE_TENSOR_CORES = 2
+ENGINES = {"auto": TT_ENGINE_AUTO, "cuda": TT_ENGINE_CUDA_CORES, "tc": TT_ENGINE_TENSOR_CORES}
 
 EXPORTS = ("tt_price_create", "tt_workspace_bytes", "tt_price_evaluate", "tt_price_prepare",
            "tt_price_run", "tt_price_results", "tt_price_transfer_bytes", "tt_price_destroy",
@@ -45,7 +49,7 @@ class tt_options(ctypes.Structure):
                 ("max_batch", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_half_sweeps", ctypes.c_int), ("sweep_tol", ctypes.c_double),
                 ("rank_tol", ctypes.c_double), ("maxvol_tol", ctypes.c_double),
-                ("block_rows", ctypes.c_int), ("device", ctypes.c_int),
+                ("block_rows", ctypes.c_int), ("engine", ctypes.c_int), ("device", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -182,7 +186,7 @@ class Pricer:
     def __init__(self, max_d: int, max_n: int, max_rank: int, max_batch: int,
                  precision: str = "fp64", device: int = 0, stream=None, max_half_sweeps: int = 0,
                  sweep_tol: float = 0.0, rank_tol: float = 0.0, maxvol_tol: float = 0.0,
-                 block_rows: int = 0, use_torch_workspace: bool = True):
+                 block_rows: int = 0, use_torch_workspace: bool = True, engine: str = "auto"):
         import torch  # device memory and streams only
 
         if not torch.cuda.is_available():
@@ -197,6 +201,7 @@ class Pricer:
         o.max_half_sweeps = max_half_sweeps
         o.sweep_tol, o.rank_tol, o.maxvol_tol = sweep_tol, rank_tol, maxvol_tol
         o.block_rows = block_rows
+        o.engine = ENGINES[engine]
         o.device = device
         with torch.cuda.device(device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(device)

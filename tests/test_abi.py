@@ -50,8 +50,13 @@ def test_create_rejects_bad_options_without_touching_the_gpu(lib):
     assert not h.value
     o.max_d, o.max_rank, o.block_rows = 4, 64, 250  # block_rows + max_rank > 256
     assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
-    # the mixed path's block product is one 128-row tensor-core tile
+    # the tensor-core block product is one 128-row tile; FP64 has no tensor-core engine
     o.max_rank, o.block_rows, o.precision = 32, 160, ttprice.TT_MIXED
+    o.engine = ttprice.TT_ENGINE_TENSOR_CORES
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    o.block_rows, o.precision = 128, ttprice.TT_FP64
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    o.engine = 3
     assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
     lib.tt_price_destroy(None)
 
@@ -62,8 +67,8 @@ def test_struct_layouts_match_c():
     #include <stddef.h>
     #include "ttprice.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu\n", sizeof(tt_options), offsetof(tt_options, sweep_tol),
-             offsetof(tt_options, block_rows), offsetof(tt_options, cuda_stream),
+      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tt_options), offsetof(tt_options, sweep_tol),
+             offsetof(tt_options, block_rows), offsetof(tt_options, engine), offsetof(tt_options, cuda_stream),
              offsetof(tt_options, workspace_bytes));
       printf("%zu %zu %zu %zu %zu\n", sizeof(tt_problem), offsetof(tt_problem, rate),
              offsetof(tt_problem, damping), offsetof(tt_problem, trunc_L), offsetof(tt_problem, seed));
@@ -81,7 +86,7 @@ def test_struct_layouts_match_c():
     T = ttprice
     want = [
         [ctypes.sizeof(T.tt_options), T.tt_options.sweep_tol.offset, T.tt_options.block_rows.offset,
-         T.tt_options.cuda_stream.offset, T.tt_options.workspace_bytes.offset],
+         T.tt_options.engine.offset, T.tt_options.cuda_stream.offset, T.tt_options.workspace_bytes.offset],
         [ctypes.sizeof(T.tt_problem), T.tt_problem.rate.offset, T.tt_problem.damping.offset,
          T.tt_problem.trunc_L.offset, T.tt_problem.seed.offset],
         [ctypes.sizeof(T.tt_diag), T.tt_diag.evaluations.offset, T.tt_diag.fail_step.offset,

@@ -42,15 +42,17 @@ def batch():
     return inputs.mixed_batch(4096)
 
 
-def _run(tp, problems, precision):
-    pr = tp.Pricer(max_d=10, max_n=256, max_rank=32, max_batch=len(problems), precision=precision)
+def _run(tp, problems, precision, engine="auto"):
+    pr = tp.Pricer(max_d=10, max_n=256, max_rank=32, max_batch=len(problems), precision=precision,
+                   engine=engine)
     rc, prices, diags = pr.evaluate(problems)
     pr.close()
     return rc, prices, diags
 
 
-def test_full_heterogeneous_batch_mixed(tp, batch):
-    rc, prices, diags = _run(tp, batch, "mixed")
+@pytest.mark.parametrize("engine", ["cuda", "tc"])
+def test_full_heterogeneous_batch_mixed(tp, batch, engine):
+    rc, prices, diags = _run(tp, batch, "mixed", engine)
     status = np.array([d.status for d in diags])
     assert np.all((status == tp.TT_OK) | (status == tp.TT_WARN_NOT_CONVERGED))
     assert np.all(np.isfinite(prices)) and np.all(prices > 0)

@@ -19,6 +19,8 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-6
 MIXED_TOL = 1e-4
+# the mixed path's maxvol block product: FP32 on CUDA cores, or 3xTF32 on tensor cores
+ENGINES = ["cuda", "tc"]
 
 
 @pytest.fixture(scope="module")
@@ -92,12 +94,13 @@ def test_ragged_blocks_with_small_block_rows(tp):
     assert abs(prices[0] / ref - 1) < FP64_TOL
 
 
-def test_mixed_ragged_blocks_and_small_ranks(tp):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_mixed_ragged_blocks_and_small_ranks(tp, engine):
     """The tensor-core block product with a ragged 16-row tail (zero-padded to the
     128-row tile) and ranks below 16 (K and N padded to 16): rank 12 over 37^3
     and rank 8 over 50^3 in blocks of 64 rows, against the FP64 oracle."""
     for p, b in [(small_problem(3, 37, 12, seed=0), 128), (small_problem(3, 50, 8), 64)]:
-        rc, prices, diags = gpu_price(tp, [p], precision="mixed", block_rows=b)
+        rc, prices, diags = gpu_price(tp, [p], precision="mixed", block_rows=b, engine=engine)
         assert diags[0].status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
         ref = ttcross.tt_price(p, ttcross.CrossOptions(block_rows=b, theta=1e-5, sweep_tol=1e-4))[0]
         assert abs(prices[0] / ref - 1) < 5e-3, (p.n_grid, b)
@@ -165,18 +168,20 @@ def test_empty_batch(tp):
     assert rc == tp.TT_OK and prices.size == 0
 
 
-def test_mixed_precision_two_asset(tp):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_mixed_precision_two_asset(tp, engine):
     """At rank 32 the train is converged (TT error ~1e-9), so the FP32 path, whose
     pivot decisions may part from FP64 at near-ties, must land within 1e-4."""
     p = inputs.two_asset_min_call(max_rank=32)
-    rc, prices, diags = gpu_price(tp, [p], precision="mixed")
+    rc, prices, diags = gpu_price(tp, [p], precision="mixed", engine=engine)
     assert diags[0].status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
     assert abs(prices[0] / oracle_price(p) - 1) < MIXED_TOL
 
 
-def test_mixed_precision_small_batch(tp):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_mixed_precision_small_batch(tp, engine):
     ps = [small_problem(3, 37, 12, seed=s) for s in range(4)] + [small_problem(3, 24, 12, payoff="max")]
-    _, prices, diags = gpu_price(tp, ps, precision="mixed")
+    _, prices, diags = gpu_price(tp, ps, precision="mixed", engine=engine)
     for p, v, dg in zip(ps, prices, diags):
         assert dg.status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
         assert abs(v / oracle_price(p) - 1) < MIXED_TOL
@@ -188,10 +193,11 @@ def test_five_asset_full_size_fp64_and_mixed(tp):
     ps = inputs.five_asset_batch(2)
     refs = [oracle_price(p) for p in ps]
     _, p64, d64 = gpu_price(tp, ps, precision="fp64")
-    _, pmx, _ = gpu_price(tp, ps, precision="mixed")
+    pmx = {e: gpu_price(tp, ps, precision="mixed", engine=e)[1] for e in ENGINES}
     for i in range(len(ps)):
         assert abs(p64[i] / refs[i] - 1) < FP64_TOL
-        assert abs(pmx[i] / refs[i] - 1) < MIXED_TOL
+        for e in ENGINES:
+            assert abs(pmx[e][i] / refs[i] - 1) < MIXED_TOL, e
         sig = np.sqrt(np.diag(ps[i].cov))
         exact = closed_forms.one_factor_price(ps[i].spot, sig, 0.3, 100.0, 0.02, 1.0, "min")
         assert abs(p64[i] / exact - 1) < 1e-4
