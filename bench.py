@@ -233,8 +233,16 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     problems = workload_problems(args.batch, rank_offset=rank)
+    # launch configuration from the project's autotuner (untimed; measured on this GPU
+    # for the workload's shape), else the library defaults
+    tuned = {}
+    if not args.no_tune:
+        from paper_2203_02804_gb300 import autotune
+
+        entry = autotune.tune(args.precision, 5, 128, 32, "min")
+        tuned = {"block_rows": entry["block_rows"], "engine": entry["engine"]}
     pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=args.batch,
-                        precision=args.precision, device=local, stream=stream)
+                        precision=args.precision, device=local, stream=stream, graph=True, **tuned)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     # ---- device-resident timing: tt_price_run only ----
@@ -286,7 +294,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": workload_config(args.batch, args.precision),
+            "config": dict(workload_config(args.batch, args.precision), launch="cuda-graph",
+                           tuned=tuned or "defaults"),
             "roofline": {"bound": "alu", "achieved": achieved,
                          "peak": FP32_PEAK_TFLOPS if args.precision == "mixed" else 1.26,
                          "unit": "TFLOP/s",
@@ -327,6 +336,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -79,6 +79,11 @@ typedef struct {
   int engine;           /* tt_engine of the maxvol block product B = A P^{-1};
                            TT_ENGINE_AUTO picks CUDA cores up to max_rank 32 and
                            tensor cores above; TT_FP64 always uses CUDA cores    */
+  int graph;            /* 1: tt_price_run replays a CUDA graph of its launches
+                           (counter reset, TT-cross kernel, finalize), captured
+                           once per batch layout on a stream the pricer owns and
+                           ordered after / before cuda_stream by events; 0: plain
+                           launches on cuda_stream                               */
   int device;           /* CUDA device ordinal                                     */
   void* cuda_stream;    /* cudaStream_t to run on; NULL = legacy default stream    */
   void* workspace;      /* optional device buffer of tt_workspace_bytes() bytes,

@@ -300,6 +300,7 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.block_rows == 0) o.block_rows = 128;
   if (o.block_rows < o.max_rank || o.block_rows + o.max_rank > ttp::kThreads) return false;
   if (o.engine < TT_ENGINE_AUTO || o.engine > TT_ENGINE_TENSOR_CORES) return false;
+  if (o.graph != 0 && o.graph != 1) return false;
   if (o.precision == TT_FP64) {
     if (o.engine == TT_ENGINE_TENSOR_CORES) return false;  // no FP64 tensor-core product
     o.engine = TT_ENGINE_CUDA_CORES;
@@ -536,6 +537,12 @@ struct tt_pricer {
   int count, njobs;
   size_t p_jobs, p_params, p_order, p_first, p_count, p_hstatus, p_bytes;  // packed offsets
   size_t last_h2d, last_d2h;
+  // graph replay (options.graph): the capture stream, ordering events, the
+  // instantiated graph and the batch layout it was captured for
+  cudaStream_t cap;
+  cudaEvent_t ev_in, ev_out;
+  cudaGraphExec_t gexec;
+  size_t gkey[8];
 };
 
 namespace {
@@ -699,7 +706,7 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   return TT_OK;
 }
 
-int run_impl(tt_pricer* h) {
+int launch_all(tt_pricer* h, cudaStream_t stream) {
   char* st = h->ws + h->dl.stage;
   const JobDesc* jobs = reinterpret_cast<const JobDesc*>(st + h->p_jobs);
   const double* params = reinterpret_cast<const double*>(st + h->p_params);
@@ -711,25 +718,61 @@ int run_impl(tt_pricer* h) {
   JobResult* jres = reinterpret_cast<JobResult*>(h->ws + h->dl.jres);
   InstanceResult* ires = reinterpret_cast<InstanceResult*>(h->ws + h->dl.ires);
   char* scratch = h->ws + h->dl.scratch;
-  if (cudaMemsetAsync(counter, 0, sizeof(int), h->stream) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaMemsetAsync(counter, 0, sizeof(int), stream) != cudaSuccess) return TT_ERR_CUDA;
   if (h->njobs > 0) {
     const int grid = std::min(h->grid, h->njobs);
     if (h->R.o.precision == TT_FP64)
-      ttp::tt_cross_kernel<double, false><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+      ttp::tt_cross_kernel<double, false><<<grid, ttp::kThreads, h->sml.total, stream>>>(
           jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
     else if (h->R.o.engine == TT_ENGINE_TENSOR_CORES)
-      ttp::tt_cross_kernel<float, true><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+      ttp::tt_cross_kernel<float, true><<<grid, ttp::kThreads, h->sml.total, stream>>>(
           jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
     else
-      ttp::tt_cross_kernel<float, false><<<grid, ttp::kThreads, h->sml.total, h->stream>>>(
+      ttp::tt_cross_kernel<float, false><<<grid, ttp::kThreads, h->sml.total, stream>>>(
           jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
     if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
   }
   if (h->count > 0) {
-    ttp::finalize_kernel<<<(h->count + 127) / 128, 128, 0, h->stream>>>(jobs, jres, first, cnt, hstat,
+    ttp::finalize_kernel<<<(h->count + 127) / 128, 128, 0, stream>>>(jobs, jres, first, cnt, hstat,
                                                                           h->count, ires);
     if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
   }
+  return TT_OK;
+}
+
+// graph replay: re-captured whenever the batch layout (job and problem counts,
+// packed offsets) differs from the captured one
+int run_impl(tt_pricer* h) {
+  if (!h->R.o.graph) return launch_all(h, h->stream);
+  const size_t key[8] = {(size_t)h->njobs, (size_t)h->count, h->p_jobs, h->p_params,
+                         h->p_order, h->p_first, h->p_count, h->p_hstatus};
+  if (!h->gexec || std::memcmp(key, h->gkey, sizeof(key)) != 0) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return TT_ERR_CUDA;
+    const int rc = launch_all(h, h->cap);
+    const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (rc != TT_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return TT_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->gexec = nullptr;
+      cudaGetLastError();
+      return TT_ERR_CUDA;
+    }
+    std::memcpy(h->gkey, key, sizeof(key));
+  }
+  if (cudaEventRecord(h->ev_in, h->stream) != cudaSuccess || cudaStreamWaitEvent(h->cap, h->ev_in, 0) != cudaSuccess ||
+      cudaGraphLaunch(h->gexec, h->cap) != cudaSuccess || cudaEventRecord(h->ev_out, h->cap) != cudaSuccess ||
+      cudaStreamWaitEvent(h->stream, h->ev_out, 0) != cudaSuccess)
+    return TT_ERR_CUDA;
   return TT_OK;
 }
 
@@ -824,6 +867,17 @@ int tt_price_create(const tt_options* opt, tt_pricer** out) {
   h->h_ires = nullptr;
   h->p_jobs = h->p_params = h->p_order = h->p_first = h->p_count = h->p_hstatus = h->p_bytes = 0;
   h->last_h2d = h->last_d2h = 0;
+  h->cap = nullptr;
+  h->ev_in = h->ev_out = nullptr;
+  h->gexec = nullptr;
+  std::memset(h->gkey, 0, sizeof(h->gkey));
+  if (R.o.graph && (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    tt_price_destroy(h);
+    return TT_ERR_CUDA;
+  }
   if (cudaMallocHost(&h->h_stage, h->dl.stage_bytes) != cudaSuccess ||
       cudaMallocHost(&h->h_pack, h->dl.stage_bytes) != cudaSuccess ||
       cudaMallocHost(&h->h_ires, sizeof(InstanceResult) * R.o.max_batch) != cudaSuccess) {
@@ -869,6 +923,11 @@ void tt_price_destroy(tt_pricer* h) {
   cudaSetDevice(h->R.o.device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  if (h->cap) cudaStreamSynchronize(h->cap);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->h_pack) cudaFreeHost(h->h_pack);

@@ -122,6 +122,23 @@ def mixed_batch(count, index=2, d_range=(3, 10), grids=(64, 128, 256), ranks=(8,
     return out
 
 
+def tuning_batch(count, d, n_grid, max_rank, payoff="min", index=4):
+    """Synthetic batch of one workload shape for the autotuner: S0_j~U[90,110],
+    sigma_j~U[0.15,0.35], equicorrelation 0.3, K=100, r=0.02, T=1, L=40,
+    alpha_j = -1.5 up to d = 10 and -5/d above (as the high-d workload)."""
+    rng = np.random.default_rng(SEED_BASE + 1000 * index + 17 * d + n_grid + max_rank)
+    alpha = -1.5 if d <= 10 else -5.0 / d
+    out = []
+    for n in range(count):
+        spot = rng.uniform(90.0, 110.0, d)
+        sigma = rng.uniform(0.15, 0.35, d)
+        out.append(Problem(spot=spot, cov=cov_from(sigma, equicorrelation(d, 0.3)), rate=0.02,
+                           maturity=1.0, strike=100.0, payoff=payoff, damping=np.full(d, alpha),
+                           n_grid=n_grid, trunc_L=40.0, max_rank=max_rank,
+                           seed=SEED_BASE + 1000 * index + n, meta={"workload": "tuning"}))
+    return out
+
+
 def random_correlation(d, rng):
     """C = D^{-1/2} A D^{-1/2} with A = W W^T / d + 0.5 I, W Gaussian d x d."""
     w = rng.standard_normal((d, d))

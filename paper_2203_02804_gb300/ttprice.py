@@ -49,7 +49,8 @@ class tt_options(ctypes.Structure):
                 ("max_batch", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_half_sweeps", ctypes.c_int), ("sweep_tol", ctypes.c_double),
                 ("rank_tol", ctypes.c_double), ("maxvol_tol", ctypes.c_double),
-                ("block_rows", ctypes.c_int), ("engine", ctypes.c_int), ("device", ctypes.c_int),
+                ("block_rows", ctypes.c_int), ("engine", ctypes.c_int), ("graph", ctypes.c_int),
+                ("device", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -186,7 +187,8 @@ class Pricer:
     def __init__(self, max_d: int, max_n: int, max_rank: int, max_batch: int,
                  precision: str = "fp64", device: int = 0, stream=None, max_half_sweeps: int = 0,
                  sweep_tol: float = 0.0, rank_tol: float = 0.0, maxvol_tol: float = 0.0,
-                 block_rows: int = 0, use_torch_workspace: bool = True, engine: str = "auto"):
+                 block_rows: int = 0, use_torch_workspace: bool = True, engine: str = "auto",
+                 graph: bool = True):
         import torch  # device memory and streams only
 
         if not torch.cuda.is_available():
@@ -202,6 +204,7 @@ class Pricer:
         o.sweep_tol, o.rank_tol, o.maxvol_tol = sweep_tol, rank_tol, maxvol_tol
         o.block_rows = block_rows
         o.engine = ENGINES[engine]
+        o.graph = 1 if graph else 0
         o.device = device
         with torch.cuda.device(device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(device)
@@ -221,6 +224,16 @@ class Pricer:
             raise RuntimeError(f"tt_price_create failed: {status_string(rc)} ({rc})")
         self.handle = h
         self._batch = None
+
+    @classmethod
+    def tuned(cls, max_d: int, max_n: int, max_rank: int, max_batch: int, precision: str = "mixed",
+              payoff: str = "min", **kw) -> "Pricer":
+        """A pricer with the autotuner's configuration for this shape (paper_2203_02804_gb300.autotune),
+        or the defaults when the shape has not been tuned."""
+        from . import autotune
+
+        cfg = autotune.lookup(precision, max_d, max_n, max_rank, payoff) or {}
+        return cls(max_d, max_n, max_rank, max_batch, precision=precision, **{**cfg, **kw})
 
     def close(self):
         if getattr(self, "handle", None):

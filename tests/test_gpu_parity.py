@@ -161,6 +161,27 @@ def test_invalid_problems_get_status_and_nan(tp):
     assert rc == tp.TT_ERR_CAPACITY or rc < 0
 
 
+def test_graph_replay_matches_plain_launches(tp):
+    """tt_price_run through a captured CUDA graph (re-captured when the batch layout
+    changes, replayed when it repeats) gives the plain launches' prices bitwise."""
+    a = [small_problem(3, 16, 4, seed=s) for s in range(3)]
+    b = [small_problem(3, 20, 5, seed=s) for s in range(5)]
+    out = {}
+    for graph in (False, True):
+        pr = tp.Pricer(max_d=3, max_n=20, max_rank=5, max_batch=8, precision="mixed", graph=graph)
+        got = []
+        for batch in (a, b, a, a):
+            pr.prepare(batch)
+            assert pr.run() == tp.TT_OK
+            rc, prices, _ = pr.results()
+            got.append(prices)
+        pr.close()
+        out[graph] = got
+    for x, y in zip(out[False], out[True]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(out[True][0], out[True][2]) and np.array_equal(out[True][2], out[True][3])
+
+
 def test_empty_batch(tp):
     pr = tp.Pricer(max_d=2, max_n=16, max_rank=4, max_batch=4, precision="fp64")
     rc, prices, diags = pr.evaluate([])
