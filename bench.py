@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -206,6 +208,57 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measure_surrogate(args, tuned):
+    """The learned surrogate on the d=5 min-call parameter box: TT prices of a seeded
+    training set (the mixed pricer), an ensemble of 4 trained by the library's kernels,
+    then on 4096 held-out problems its error against the TT prices, the share of quotes
+    it serves at a member spread of 1e-4 and 1e-3 (the rest go back to TT), and the
+    device throughput of ensemble inference (features resident, CUDA events)."""
+    import torch
+
+    from paper_2203_02804_gb300 import inputs, surrogate as sg, ttprice
+
+    train_ps = inputs.surrogate_batch(args.surrogate_samples, index=5)
+    held = inputs.surrogate_batch(4096, index=6)
+    spr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=max(len(train_ps), len(held)),
+                         precision="mixed", graph=True, **tuned)
+    t0 = time.perf_counter()
+    _, y_train, _ = spr.evaluate(train_ps)
+    data_s = time.perf_counter() - t0
+    _, y_held, _ = spr.evaluate(held)
+    spr.close()
+    s = sg.Surrogate(members=4, seed=11)
+    t0 = time.perf_counter()
+    s.fit(train_ps, y_train, epochs=args.surrogate_epochs, batch=1024)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    mean, spread = s.predict_log(held)
+    k = np.array([p.strike for p in held])
+    err = np.abs(k * np.exp(mean) / y_held - 1.0)
+    out = {"members": 4, "train_samples": len(train_ps), "epochs": args.surrogate_epochs,
+           "tt_data_s": data_s, "train_s": fit_s, "held_out": len(held),
+           "median_rel_err": float(np.median(err)), "p99_rel_err": float(np.quantile(err, 0.99))}
+    for tol in (1e-4, 1e-3, 1e-2):
+        served = spread <= tol
+        out[f"served_at_{tol:g}"] = float(served.mean())
+        out[f"max_err_served_{tol:g}"] = float(err[served].max()) if served.any() else None
+    x = s.standardise(held)
+    x = x.repeat(64, 1).contiguous()  # 262,144 quotes
+    for _ in range(2):
+        s.predict_device(x)
+    st = s.nets[0].stream
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    reps = 5
+    for _ in range(reps):
+        s.predict_device(x)
+    b.record(st)
+    torch.cuda.synchronize()
+    out["quotes_per_s"] = reps * x.shape[0] / (a.elapsed_time(b) / 1e3)
+    out["unit"] = "quotes/s (ensemble of 4, bfloat16 weights, features resident)"
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -284,6 +337,9 @@ def run_gpu(args):
     e2e_s = max_over_ranks(e2e_s, dist)
     e2e_value = args.batch * world * args.steps / e2e_s
     pr.close()
+    surrogate = None
+    if args.surrogate_samples > 0 and world == 1:
+        surrogate = measure_surrogate(args, tuned)
 
     if rank == 0:
         clocks = clk.summary()
@@ -311,6 +367,8 @@ def run_gpu(args):
             "status_counts": {str(s): sum(1 for d in diags if d.status == s)
                               for s in sorted({d.status for d in diags})},
         }
+        if surrogate is not None:
+            line["surrogate"] = surrogate
         if sample is not None:
             sp, sprices, sdt, workers = sample
             n = len(sp)
@@ -337,6 +395,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--surrogate-samples", type=int, default=1 << 18,
+                    help="TT-priced training samples of the learned surrogate (0: skip it)")
+    ap.add_argument("--surrogate-epochs", type=int, default=24)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -20,6 +20,9 @@ Modules
                    contract it with the quadrature weights (Section IV)
   splitmix      -- the SplitMix64 counter-based generator (Steele, Lea and
                    Flood 2014) used to draw the random initial pivots
+  mlp           -- the learned surrogate's network in FP64: fully connected
+                   layers with SiLU, their backward pass, MSE and Adam
+                   (Kingma and Ba 2015); no counterpart in the paper
 
 Parity status of every function is stated in its docstring; no function here
 is "parity unpinned": each is pinned by a test in tests/test_oracle_*.py

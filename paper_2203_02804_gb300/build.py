@@ -18,8 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libttprice.so")
-SOURCES = ["ttprice.cu"]
-DEPS = ["ttprice.cu", "ttprice_device.cuh", "ttprice_kernels.cuh"]
+SOURCES = ["ttprice.cu", "mlp.cu"]
+DEPS = ["ttprice.cu", "ttprice_device.cuh", "ttprice_kernels.cuh", "ttprice_tc.cuh", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,17 +38,27 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    deps = [os.path.join(CSRC, f) for f in DEPS] + [os.path.join(INCLUDE, "ttprice.h")]
+    """Compile the sources to objects in parallel, then link the shared library."""
+    deps = [os.path.join(CSRC, f) for f in DEPS] + [os.path.join(INCLUDE, h) for h in ("ttprice.h", "ttmlp.h")]
     if not force and not _stale(LIB, deps):
         return LIB
+    objs, procs = [], []
+    for s in SOURCES:
+        obj = os.path.join(CSRC, os.path.splitext(s)[0] + ".o")
+        cmd = [nvcc_path(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+               "-I", INCLUDE, "-c", "-o", obj, os.path.join(CSRC, s)]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+            print(" ".join(cmd), flush=True)
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    failed = [p.wait() for p in procs]
+    if any(failed):
+        raise subprocess.CalledProcessError(max(failed), "nvcc")
     tmp = LIB + ".tmp"
-    cmd = [nvcc_path(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC", "-I", INCLUDE, "-o", tmp,
-           *[os.path.join(CSRC, s) for s in SOURCES]]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
+    subprocess.run([nvcc_path(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

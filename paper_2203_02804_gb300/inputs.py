@@ -122,6 +122,28 @@ def mixed_batch(count, index=2, d_range=(3, 10), grids=(64, 128, 256), ranks=(8,
     return out
 
 
+def surrogate_batch(count, index=5, n_grid=128, trunc_L=40.0, max_rank=32):
+    """d=5 calls on the minimum spread over a parameter box, for the learned
+    surrogate: S0_j~U[90,110], sigma_j~U[0.15,0.35], equicorrelation rho~U[0,0.6],
+    K~U[90,110], T~U[0.5,1.5], r~U[0,0.05], alpha~U[-2,-1.2] (same on every axis),
+    N=128 on [-40,40], rank 32."""
+    rng = np.random.default_rng(SEED_BASE + index)
+    out = []
+    for n in range(count):
+        spot = rng.uniform(90.0, 110.0, 5)
+        sigma = rng.uniform(0.15, 0.35, 5)
+        rho = float(rng.uniform(0.0, 0.6))
+        strike = float(rng.uniform(90.0, 110.0))
+        maturity = float(rng.uniform(0.5, 1.5))
+        rate = float(rng.uniform(0.0, 0.05))
+        alpha = float(rng.uniform(-2.0, -1.2))
+        out.append(Problem(spot=spot, cov=cov_from(sigma, equicorrelation(5, rho)), rate=rate,
+                           maturity=maturity, strike=strike, payoff="min", damping=np.full(5, alpha),
+                           n_grid=n_grid, trunc_L=trunc_L, max_rank=max_rank,
+                           seed=SEED_BASE + 1000 * index + n, meta={"workload": "surrogate"}))
+    return out
+
+
 def tuning_batch(count, d, n_grid, max_rank, payoff="min", index=4):
     """Synthetic batch of one workload shape for the autotuner: S0_j~U[90,110],
     sigma_j~U[0.15,0.35], equicorrelation 0.3, K=100, r=0.02, T=1, L=40,

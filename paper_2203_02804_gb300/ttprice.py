@@ -35,7 +35,10 @@ ENGINES = {"auto": TT_ENGINE_AUTO, "cuda": TT_ENGINE_CUDA_CORES, "tc": TT_ENGINE
 
 EXPORTS = ("tt_price_create", "tt_workspace_bytes", "tt_price_evaluate", "tt_price_prepare",
            "tt_price_run", "tt_price_results", "tt_price_transfer_bytes", "tt_price_destroy",
-           "tt_status_string", "tt_price_evaluate_static")
+           "tt_status_string", "tt_price_evaluate_static",
+           # the surrogate's network kernels (include/ttmlp.h)
+           "tt_mlp_forward", "tt_mlp_forward_bf16", "tt_mlp_backward", "tt_mlp_mse", "tt_mlp_adam",
+           "tt_mlp_to_bf16", "tt_mlp_ensemble", "tt_mlp_gather")
 
 # limits of tt_price_evaluate_static (include/ttprice.h)
 TT_STATIC_MAX_BATCH = 64

@@ -1,6 +1,7 @@
 """The C ABI on the CPU: the library builds for sm_103a, loads, exports every
-function include/ttprice.h declares, and the ctypes mirrors of its structs have
-the C layout (checked against gcc).  No compute call runs here."""
+function include/ttprice.h and include/ttmlp.h declare, and the ctypes mirrors
+of its structs have the C layout (checked against gcc).  No compute call runs
+here."""
 import ctypes
 import os
 import re
@@ -13,6 +14,7 @@ from paper_2203_02804_gb300 import build, ttprice
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "ttprice.h")
+HEADERS = [HEADER, os.path.join(ROOT, "include", "ttmlp.h")]
 
 
 @pytest.fixture(scope="module")
@@ -22,9 +24,11 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tt_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(tt_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
