@@ -109,58 +109,72 @@ __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, doubl
   }
   if (lane == 0) dscr[16 + warp] = part;
   // initial right index sets, one thread per bond
-  for (int k = 1 + tid; k < d; k += kThreads) {
+  // one warp per core k; lanes draw slots (first attempts) or coordinates (redraws) in
+  // parallel, duplicates are resolved slot by slot in order, so the accepted sets
+  // are those of a plain sequential draw
+  for (int k = 1 + warp; k < d; k += kWarps) {
     const int width = d - k;
     const long long cap = jd.rmax;
     long long rk = ipow_cap(n, k, cap + 1);
     rk = rk < cap ? rk : cap;
     const long long nw = ipow_cap(n, width, cap + 1);
     if (nw < rk) rk = nw;
-    x.rsz[k] = (int)rk;
+    if (lane == 0) x.rsz[k] = (int)rk;
     if (nw == rk) {  // every right multi-index, lexicographic
-      for (int b = 0; b < rk; ++b) {
-        uint16_t* dst = rset_at(x, k, b);
-        int rem = b;
+      for (int bb = lane; bb < rk; bb += 32) {
+        uint16_t* dst = rset_at(x, k, bb);
+        int rem = bb;
         for (int pos = width - 1; pos >= 0; --pos) {
           dst[pos] = (uint16_t)(rem % n);
           rem /= n;
         }
       }
     } else {
+      // coordinate pos of slot bb at attempt t (around the centre for the first
+      // kPeakAttempts attempts, uniform after); every FP64 operation rounded
+      // separately (no contraction) so the draw is reproducible
+      auto coord = [&](int bb, int t, int pos) -> uint16_t {
+        const int j = k + pos;
+        if (t < kPeakAttempts) {
+          const double w = __ddiv_rn(1.5, __dmul_rn(__dsqrt_rn(__dmul_rn(prm[j * d + j], jd.T)), eta));
+          double sum = 0.0;
+          for (int qq = 0; qq < 4; ++qq) {
+            const unsigned long long h = splitmix64(pivot_key(jd.seed, jd.term, k, t, bb, 4 * j + qq));
+            sum = __dadd_rn(sum, __dmul_rn((double)(h >> 11), 0x1p-53));
+          }
+          const double z = __dmul_rn(__dsub_rn(sum, 2.0), 1.7320508075688772);
+          long long idx = n / 2 + (long long)floor(__dadd_rn(__dmul_rn(w, z), 0.5));
+          idx = idx < 0 ? 0 : (idx > n - 1 ? n - 1 : idx);
+          return (uint16_t)idx;
+        }
+        return (uint16_t)(splitmix64(pivot_key(jd.seed, jd.term, k, t, bb, j)) % n);
+      };
       uint16_t* c0 = rset_at(x, k, 0);
-      for (int pos = 0; pos < width; ++pos) c0[pos] = (uint16_t)(n / 2);
-      for (int b = 1; b < rk; ++b) {
-        uint16_t* dst = rset_at(x, k, b);
+      for (int pos = lane; pos < width; pos += 32) c0[pos] = (uint16_t)(n / 2);
+      for (int bb = 1 + lane; bb < rk; bb += 32) {
+        uint16_t* dst = rset_at(x, k, bb);
+        for (int pos = 0; pos < width; ++pos) dst[pos] = coord(bb, 0, pos);
+      }
+      __syncwarp();
+      for (int bb = 1; bb < rk; ++bb) {
+        uint16_t* dst = rset_at(x, k, bb);
         bool fresh = false;
         for (int t = 0; t < 65536 && !fresh; ++t) {
-          for (int pos = 0; pos < width; ++pos) {
-            const int j = k + pos;
-            if (t < kPeakAttempts) {
-              // around the centre, spread w_j = 1.5/(sqrt(Cov_jj T) eta) grid steps; every
-              // operation rounded separately (no contraction) so the draw is reproducible
-              const double w = __ddiv_rn(1.5, __dmul_rn(__dsqrt_rn(__dmul_rn(prm[j * d + j], jd.T)), eta));
-              double sum = 0.0;
-              for (int qq = 0; qq < 4; ++qq) {
-                const unsigned long long h = splitmix64(pivot_key(jd.seed, jd.term, k, t, b, 4 * j + qq));
-                sum = __dadd_rn(sum, __dmul_rn((double)(h >> 11), 0x1p-53));
-              }
-              const double z = __dmul_rn(__dsub_rn(sum, 2.0), 1.7320508075688772);
-              long long idx = n / 2 + (long long)floor(__dadd_rn(__dmul_rn(w, z), 0.5));
-              idx = idx < 0 ? 0 : (idx > n - 1 ? n - 1 : idx);
-              dst[pos] = (uint16_t)idx;
-            } else {
-              dst[pos] = (uint16_t)(splitmix64(pivot_key(jd.seed, jd.term, k, t, b, j)) % n);
-            }
+          if (t > 0) {
+            for (int pos = lane; pos < width; pos += 32) dst[pos] = coord(bb, t, pos);
+            __syncwarp();
           }
-          fresh = true;
-          for (int bb = 0; bb < b && fresh; ++bb) {
-            const uint16_t* o = rset_at(x, k, bb);
+          bool dup = false;
+          for (int q = lane; q < bb && !dup; q += 32) {
+            const uint16_t* o = rset_at(x, k, q);
             bool same = true;
             for (int pos = 0; pos < width && same; ++pos) same = (o[pos] == dst[pos]);
-            fresh = !same;
+            dup = same;
           }
+          fresh = !__any_sync(0xffffffffu, dup);
         }
-        if (!fresh) x.misc[MISC_DRAW] = 1;
+        if (!fresh && lane == 0) x.misc[MISC_DRAW] = 1;
+        __syncwarp();
       }
     }
   }
