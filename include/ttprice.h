@@ -120,7 +120,10 @@ typedef struct {
   int fail_step;         /* for TT_ERR_NUMERIC: 1 fiber of rank 0, 2 singular pivot
                             block in maxvol, 3 singular interpolation solve,
                             4 non-finite estimate; 5 initial pivots not drawable;
-                            6 a tensor-core block product did not complete (mixed) */
+                            6 a tensor-core block product did not complete (mixed);
+                            with TT_WARN_NOT_CONVERGED: 7 the mixed path stopped at a
+                            half-sweep whose estimate moved by over 100x the previous
+                            one and reports that previous estimate               */
   int maxvol_rollbacks;  /* cores whose maxvol returned to its last verified pivot set
                             after the working-precision pivot block became singular */
   double imag_part;      /* Im of the discrete sum; 0 up to the TT error           */

@@ -15,8 +15,8 @@ What the paper fixes (Section IV.A-B) and what is read into it
       - initial rows: Gaussian elimination with partial pivoting (GEPP) run as a
         flat tournament: the current winners are stacked on top of the next
         candidates and GEPP keeps the pivot rows.  Candidates are the next block
-        of ``block_rows`` rows for fibers of at most 256 rows; larger fibers are
-        screened in blocks of 512 rows, each 64-row sub-block offering its 16
+        of ``block_rows`` rows for fibers of at most 512 rows; larger fibers are
+        screened in blocks of 1024 rows, each 128-row sub-block offering its 16
         rows with the largest entries.  A column whose best pivot is at most
         ``theta`` times that column's largest entry is skipped (numerically
         dependent); the pivot block of the winners then drops the columns
@@ -178,14 +178,14 @@ def gepp_select(c_mat, theta):
     return rows, cols
 
 
-SCREEN_MIN_ROWS = 256   # fibers with more rows than this are screened
-SCREEN_BLOCK = 512      # rows per screening block (one GEPP merge each)
-SCREEN_SUB = 64         # rows per sub-block
-SCREEN_KEEP = 16        # rows each sub-block keeps (a fiber of more than 256 rows offers >= 64)
+SCREEN_MIN_ROWS = 512   # fibers with more rows than this are screened
+SCREEN_BLOCK = 1024     # rows per screening block (one GEPP merge each)
+SCREEN_SUB = 128        # rows per sub-block
+SCREEN_KEEP = 16        # rows each sub-block keeps (a fiber of more than 512 rows offers >= 64)
 
 
 def screen_rows(a_mat, start, stop):
-    """Candidates of one screening block: in every 64-row sub-block, the 16 rows
+    """Candidates of one screening block: in every 128-row sub-block, the 16 rows
     whose largest |entry|^2 (over all columns, rounded to FP32) is largest, ties
     to the lower row; returned in ascending row order."""
     keys = (a_mat[start:stop].real ** 2 + a_mat[start:stop].imag ** 2).max(axis=1).astype(np.float32)

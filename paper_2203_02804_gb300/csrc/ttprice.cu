@@ -28,6 +28,8 @@ struct MinBlocks {
   static constexpr int value = sizeof(R) == 4 ? TTP_MIN_BLOCKS_F32 : 1;  // FP32: several CTAs per SM
 };
 
+constexpr double kBlowup = 100.0;  // FP32 half-sweep growth guard (see the sweep loop)
+
 template <typename R, bool TC>
 __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel(const JobDesc* __restrict__ jobs,
                                                             const double* __restrict__ params,
@@ -180,9 +182,20 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       }
       if (s >= 1) {
         const double dx = est.x - prev.x, dy = est.y - prev.y;
-        if (sqrt(dx * dx + dy * dy) <= kn.sweep_tol * sqrt(est.x * est.x + est.y * est.y)) {
+        const double change = sqrt(dx * dx + dy * dy);
+        if (change <= kn.sweep_tol * sqrt(est.x * est.x + est.y * est.y)) {
           status = ST_OK;
           break;
+        }
+        // FP32 guard: a half-sweep whose estimate moves by more than kBlowup times the
+        // previous one has followed a drifted P^{-1} into an ill-conditioned pivot
+        // block; keep the previous estimate and stop (reported as not converged)
+        if constexpr (sizeof(R) == 4) {
+          if (change > kBlowup * sqrt(prev.x * prev.x + prev.y * prev.y)) {
+            est = prev;
+            if (tid == 0) x.fail_step = 7;
+            break;
+          }
         }
       }
       prev = est;

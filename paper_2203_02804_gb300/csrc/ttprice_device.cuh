@@ -532,19 +532,21 @@ __device__ __forceinline__ void eval_prow(Ctx<R>& x, int j, int g, int rho) {
 // form one merge, whose candidates are, from each kScreenSub-row sub-block, the
 // kScreenKeep rows with the largest max_c |a_rc|^2 (rounded to FP32; ties to the
 // lower row), in ascending row order.  One warp screens one sub-block.
-constexpr int kScreenMinRows = 256;
-constexpr int kScreenBlock = 512;
-constexpr int kScreenSub = 64;
+constexpr int kScreenMinRows = 512;  // larger fibers offer >= 4 full sub-blocks: 64 candidates
+constexpr int kScreenBlock = 1024;
+constexpr int kScreenSub = 128;
 constexpr int kScreenKeep = 16;
+constexpr int kScreenRpl = kScreenSub / 32;  // rows per lane
+static_assert(kScreenBlock == kWarps * kScreenSub, "one warp per sub-block");
 
 template <typename R>
 __device__ int screen_block(Ctx<R>& x, int ss, int se, int nc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = x.n;
   const int base = ss + warp * kScreenSub;
-  float key[2];
-  bool valid[2];
+  float key[kScreenRpl];
+  bool valid[kScreenRpl];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < kScreenRpl; ++h) {
     const int r = base + lane + 32 * h;
     valid[h] = r < se;
     key[h] = 0.0f;
@@ -554,26 +556,40 @@ __device__ int screen_block(Ctx<R>& x, int ss, int se, int nc) {
       key[h] = (float)mx;
     }
   }
-  // warp top-kScreenKeep: repeated argmax; the kept set is a 64-bit row mask
-  unsigned long long kept = 0ull;
-  bool taken[2] = {false, false};
+  // warp top-kScreenKeep: repeated argmax; the kept set is a row mask, 32 rows per word
+  unsigned kept[kScreenRpl];
+  bool taken[kScreenRpl];
+#pragma unroll
+  for (int h = 0; h < kScreenRpl; ++h) {
+    kept[h] = 0u;
+    taken[h] = false;
+  }
   for (int t = 0; t < kScreenKeep; ++t) {
     float v = -1.0f;
     int vi = INT_MAX;
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < kScreenRpl; ++h)
       if (valid[h] && !taken[h]) am_merge(v, vi, key[h], lane + 32 * h);
     warp_argmax(v, vi);
     if (vi == INT_MAX) break;
-    kept |= 1ull << vi;
-    if ((vi & 31) == lane) taken[vi >> 5] = true;
+#pragma unroll
+    for (int h = 0; h < kScreenRpl; ++h)
+      if ((vi >> 5) == h) {
+        kept[h] |= 1u << (vi & 31);
+        if ((vi & 31) == lane) taken[h] = true;
+      }
   }
-  // write the kept rows of this sub-block in ascending order
-  const int cnt = __popcll(kept);
-  if (lane < cnt) {
-    unsigned long long msk = kept;
-    for (int q = 0; q < lane; ++q) msk &= msk - 1ull;  // drop the lane lowest set bits
-    x.scand[warp * kScreenKeep + lane] = base + __ffsll((long long)msk) - 1;
+  // write the kept rows of this sub-block in ascending order: lane q takes the q-th set bit
+  int cnt = 0;
+#pragma unroll
+  for (int h = 0; h < kScreenRpl; ++h) {
+    const int c = __popc(kept[h]);
+    if (lane >= cnt && lane < cnt + c) {
+      unsigned msk = kept[h];
+      for (int q = 0; q < lane - cnt; ++q) msk &= msk - 1u;  // drop the lowest set bits
+      x.scand[warp * kScreenKeep + lane] = base + 32 * h + __ffs((int)msk) - 1;
+    }
+    cnt += c;
   }
   if (lane == 0) x.scnt[warp] = cnt;
   __syncthreads();
