@@ -381,9 +381,9 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + cs - 1) / cs);
   const int kp = ttp::tc::pad16(r);
   const bool tcore = o.engine == TT_ENGINE_TENSOR_CORES;
-  // tensor cores: two buffers of four 128-row planes of one 8-column chunk (hi and lo
-  // parts of Re A and Im A)
-  if (tcore) sw_elems = std::max(sw_elems, 2 * 4 * ttp::tc::kRows * ttp::kTcChunk * 4 / cs);
+  // tensor cores: kTcBufs buffers of four 128-row planes of one kTcChunk-column chunk
+  // (hi and lo parts of Re A and Im A)
+  if (tcore) sw_elems = std::max(sw_elems, ttp::kTcBufs * 4 * ttp::tc::kRows * ttp::kTcChunk * 4 / cs);
   int off = 0;
   auto take = [&](int bytes) {
     int at = off;

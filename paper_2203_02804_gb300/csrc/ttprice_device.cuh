@@ -412,7 +412,8 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
 // P^{-1} of the FP32 path: hi and lo TF32 parts in K-major tensor-core planes
 // (hi in M, lo in the winner-value buffer, free during maxvol)
 // ---------------------------------------------------------------------------
-constexpr int kTcChunk = 8;  // kept columns per evaluation/MMA chunk (one K step), two buffers
+constexpr int kTcChunk = 16;               // kept columns per evaluation/MMA chunk (two K steps)
+constexpr int kTcBufs = 16 / kTcChunk;     // operand buffers in the 32 KB (1: chunk 16, 2: chunk 8)
 
 __device__ __forceinline__ float tf32_hi(float v) {
   uint32_t r;
@@ -1003,10 +1004,10 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
 // ---------------------------------------------------------------------------
 // FP32 maxvol with the block product on the tensor cores.  Same visits, swaps,
 // rollback and row sums as maxvol_refine.  Per visit the block's fiber rows at
-// the kept columns are evaluated in chunks of 8 columns into four K-major
-// planes (hi and lo TF32 parts of Re A and Im A, 128 rows zero-padded), double
-// buffered so that one chunk's products run while the next is evaluated, and
-// multiplied into TMEM with 3xTF32 products
+// the kept columns are evaluated in chunks of kTcChunk columns into four K-major
+// planes (hi and lo TF32 parts of Re A and Im A, 128 rows zero-padded; with
+// chunks of 8, two buffers let one chunk's products run while the next is
+// evaluated) and multiplied into TMEM with 3xTF32 products
 //   A P^{-1} ~ A_hi M_hi + A_hi M_lo + A_lo M_hi,
 // as two real products of N = 2 kp, D = Re A [Re M | Im M] and
 // E = Im A [Re M | Im M]; the read-back combines them, B = (D_re - E_im) +
@@ -1023,8 +1024,8 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = x.n;
   const int nb = (m + b - 1) / b;
   const int kp = tc::pad16(rho);
-  // A chunk planes: 128 rows x 8 columns, 256 bytes per 8-row group, 4 KB each;
-  // a buffer holds four (hi and lo of Re A and Im A), two buffers
+  // A chunk planes: 128 rows x kTcChunk columns, 32 kTcChunk bytes per 8-row group;
+  // a buffer holds four (hi and lo of Re A and Im A); kTcBufs buffers
   constexpr int kSboA = kTcChunk * 32, kPlaneA = (tc::kRows / 8) * kSboA, kBufA = 4 * kPlaneA;
   unsigned char* a_pl = reinterpret_cast<unsigned char*>(x.sw);
   const int sbo_m = kp * 32;
@@ -1103,15 +1104,17 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
     // barrier k, so each barrier has at most one phase outstanding.
     const int nch = kp / kTcChunk;
     for (int c = 0; c < nch && !failed; ++c) {
+      // chunk c uses buffer c % kTcBufs and completes on barrier c & 1
       const int bufk = c & 1, c0 = c * kTcChunk;
-      unsigned char* const pb = a_pl + bufk * kBufA;
+      unsigned char* const pb = a_pl + (c % kTcBufs) * kBufA;
       bool ok = true;
-      if (!frozen && c >= 2) {  // the products that last read this buffer (checked at the next barrier)
-        ok = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
-        if (ok) phase[bufk] ^= 1u;  // a phase that timed out stays the outstanding one
+      if (!frozen && c >= kTcBufs) {  // the products that last read this buffer (checked at the next barrier)
+        const int pk = (c - kTcBufs) & 1;
+        ok = tc::mbar_wait(x.mbar + pk, phase[pk]);
+        if (ok) phase[pk] ^= 1u;  // a phase that timed out stays the outstanding one
       }
       // evaluation: lane -> rows 8g + lane/4 (two row groups per warp), columns
-      // lane%4 and lane%4 + 4; a warp's store is 8 rows x 4 columns = 128 bytes
+      // lane%4 + 4jj; a warp's store is 8 rows x 4 columns = 128 bytes
       TTP_TIC(t_ev8);
 #pragma unroll
       for (int gg = 0; gg < 2; ++gg) {
@@ -1120,7 +1123,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
         const int g = rs + (live ? r : 0);
         const RowTab<R> rt = row_tab(x, g % N);
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
+        for (int jj = 0; jj < kTcChunk / 4; ++jj) {
           const int tl = (lane & 3) + 4 * jj, t = c0 + tl;
           cpx<R> v = {R(0), R(0)};
           if (live && t < rho) v = eval_row_point(x, rt, g / N, x.jp[t]);
@@ -1147,18 +1150,21 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
         // planes of P^{-1} are adjacent), each as hi*hi + hi*lo + lo*hi; a plane
         // further on is (byte offset >> 4) further in the start-address field
         const uint64_t a0 = tc::smem_desc(tc::smem_u32(pb), (uint32_t)kSboA), ap = kPlaneA >> 4;
-        const uint32_t km = (uint32_t)(c0 / 4) * 128u;
-        const uint64_t mh = tc::smem_desc(tc::smem_u32(m_hi) + km, (uint32_t)sbo_m);
-        const uint64_t ml = tc::smem_desc(tc::smem_u32(m_lo) + km, (uint32_t)sbo_m);
         const uint32_t id = tc::instr_desc(2 * kp, false);
-        const uint32_t acc = c > 0 ? 1u : 0u;
         // thread 0: D = Re A [M] into columns [0, 2kp); thread 128: E = Im A [M] into [2kp, 4kp)
         const int part = tid >> 7;
         const uint32_t dst = x.tmem + (uint32_t)(part * 2 * kp);
-        const uint64_t ahi = a0 + (uint64_t)part * ap, alo = a0 + (uint64_t)(2 + part) * ap;
-        tc::mma_tf32(dst, ahi, mh, id, acc);  // A hi * M hi
-        tc::mma_tf32(dst, ahi, ml, id, 1u);   // A hi * M lo
-        tc::mma_tf32(dst, alo, mh, id, 1u);   // A lo * M hi
+        for (int ks = 0; ks < kTcChunk / 8; ++ks) {  // K = 8 per instruction: 256 bytes along K
+          const uint32_t km = (uint32_t)(c0 / 4 + 2 * ks) * 128u;
+          const uint64_t mh = tc::smem_desc(tc::smem_u32(m_hi) + km, (uint32_t)sbo_m);
+          const uint64_t ml = tc::smem_desc(tc::smem_u32(m_lo) + km, (uint32_t)sbo_m);
+          const uint64_t ko = (uint64_t)ks * (256 >> 4);
+          const uint64_t ahi = a0 + (uint64_t)part * ap + ko, alo = a0 + (uint64_t)(2 + part) * ap + ko;
+          const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+          tc::mma_tf32(dst, ahi, mh, id, acc);  // A hi * M hi
+          tc::mma_tf32(dst, ahi, ml, id, 1u);   // A hi * M lo
+          tc::mma_tf32(dst, alo, mh, id, 1u);   // A lo * M hi
+        }
         tc::commit(x.mbar + bufk);            // the barrier expects both issuing threads
         TTP_TOC(t_mma, 11);
       }
@@ -1195,12 +1201,13 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
         }
       }
       TTP_TOC(t_rsum, 15);
-      if (frozen) __syncthreads();  // the next chunk overwrites what the row sums read
+      // the next chunk overwrites what the row sums read (with one buffer, or no products)
+      if (frozen || kTcBufs == 1) __syncthreads();
     }
     // the products of the last two chunks
     if (!frozen && !failed) {
       bool ok = true;
-      for (int c = max(0, nch - 2); c < nch; ++c) {
+      for (int c = max(0, nch - kTcBufs); c < nch; ++c) {
         const int bufk = c & 1;
         const bool done = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
         if (done) phase[bufk] ^= 1u;
