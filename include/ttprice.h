@@ -121,9 +121,16 @@ typedef struct {
                             block in maxvol, 3 singular interpolation solve,
                             4 non-finite estimate; 5 initial pivots not drawable;
                             6 a tensor-core block product did not complete (mixed);
-                            with TT_WARN_NOT_CONVERGED: 7 the mixed path stopped at a
-                            half-sweep whose estimate moved by over 100x the previous
-                            one and reports that previous estimate               */
+                            8 (mixed) no half-sweep estimate of a train was
+                            plausible (see 7) and the last one's share of the
+                            price exceeds the sum of the spots;
+                            with TT_WARN_NOT_CONVERGED: 7 the mixed path reports an
+                            earlier half-sweep's estimate of some train: the last one
+                            moved by over 100x a plausible one before it, or was not
+                            plausible itself, with an imaginary part above 1/4 of
+                            its real part (the exact grid sum is real) or a share of
+                            the price outside (0, sum of spots]; the reported one is
+                            the latest plausible one                             */
   int maxvol_rollbacks;  /* cores whose maxvol returned to its last verified pivot set
                             after the working-precision pivot block became singular */
   double imag_part;      /* Im of the discrete sum; 0 up to the TT error           */

@@ -29,6 +29,24 @@ struct MinBlocks {
 };
 
 constexpr double kBlowup = 100.0;  // FP32 half-sweep growth guard (see the sweep loop)
+constexpr double kImagTrust = 0.25;  // FP32: largest |Im| / |Re| of a reportable estimate
+
+// one job's half-sweep state (see the sweep loop)
+struct SweepState {
+  double sign, bound;  // the train's sign; cap / (weight exp(logscale + norm_sum))
+  double norm_sum;
+  double2 est;         // the estimate to report
+  double2 trusted;     // FP32: the latest plausible estimate
+  double2 hist[2];     // the last two half-sweeps' estimates, by parity
+  int have_trusted, ok_hist[2];
+};
+
+// an FP32 half-sweep estimate that can be reported: |Im| <= kImagTrust |Re| and the
+// train's share of the price, sign weight exp(logscale + norm_sum) Re, in (0, cap]
+__device__ __forceinline__ bool plausible(const SweepState& ss, double2 est) {
+  const double re = ss.sign * est.x;
+  return re > 0.0 && fabs(est.y) <= kImagTrust * re && re <= ss.bound;
+}
 
 template <typename R, bool TC>
 __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel(const JobDesc* __restrict__ jobs,
@@ -39,6 +57,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
                                                             Knobs kn) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double dscr[32];
+  __shared__ SweepState ss;
   // The context is uniform across the CTA: keeping it in shared memory (written
   // by thread 0) keeps its ~40 pointers out of every thread's registers.
   __shared__ Ctx<R> x;
@@ -144,13 +163,24 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
     job_setup(x, jd, prm, dscr, norm_sum);
     TTP_TOC(t_js, 13);
 
-    double2 est = make_double2(0.0, 0.0), prev = make_double2(0.0, 0.0);
+    // The job's sweep state is uniform across the CTA; it sits in shared memory
+    // (thread 0 writes it, the barriers of the next half-sweep publish it) rather
+    // than in registers that would stay live through the cores' loops.
+    if (tid == 0) {
+      ss.sign = jd.sign;
+      ss.bound = exp(fmin(log(jd.cap / jd.weight) - jd.logscale - norm_sum, 700.0));
+      ss.norm_sum = norm_sum;
+      ss.est = ss.trusted = ss.hist[0] = ss.hist[1] = make_double2(0.0, 0.0);
+      ss.have_trusted = 0;
+      ss.ok_hist[0] = ss.ok_hist[1] = 0;
+    }
     int status = x.misc[MISC_DRAW] ? ST_INVALID : ST_NOT_CONVERGED;
     int hs = 0, maxrank = 1;
     const int d = jd.d;
     for (int s = 0; s < kn.max_half_sweeps && status == ST_NOT_CONVERGED; ++s) {
       if (tid == 0) x.vchain[0] = make_double2(1.0, 0.0);
       __syncthreads();
+      double2 est = make_double2(0.0, 0.0);
       if ((s & 1) == 0) {
         for (int k = 0; k + 1 < d; ++k) {
           const int rho = core_select<R, TC>(x, kn, k, DIR_LR);
@@ -176,35 +206,72 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
         status = ST_NUMERIC;
         break;
       }
+      // The midpoint grid is symmetric and the payoff real, so the exact grid sum
+      // is real and |Im est| is a lower bound on the estimate's error; the train's
+      // share of the price lies in (0, sum of spots].  In FP32 a half-sweep built on
+      // poor index sets (the first one, from random pivots, or a rank-limited one)
+      // can amplify the integrand's rounding past both; such an estimate neither
+      // converges nor is reported, and the sweeps go on from its index sets.
+      bool est_ok = true;
+      if constexpr (sizeof(R) == 4) est_ok = plausible(ss, est);
+      if (tid == 0) {
+        ss.est = est;
+        if (est_ok) {
+          ss.trusted = est;
+          ss.have_trusted = 1;
+        }
+      }
       if (d == 1) {
         status = ST_OK;
         break;
       }
+      // the previous estimate: written at s - 1 into slot (s - 1) & 1; slot s & 1 is
+      // written below, while other threads may still read this one
+      const double2 prev = ss.hist[(s + 1) & 1];
+      const bool prev_ok = ss.ok_hist[(s + 1) & 1];
       if (s >= 1) {
         const double dx = est.x - prev.x, dy = est.y - prev.y;
         const double change = sqrt(dx * dx + dy * dy);
-        if (change <= kn.sweep_tol * sqrt(est.x * est.x + est.y * est.y)) {
+        if (est_ok && change <= kn.sweep_tol * sqrt(est.x * est.x + est.y * est.y)) {
           status = ST_OK;
           break;
         }
-        // FP32 guard: a half-sweep whose estimate moves by more than kBlowup times the
-        // previous one has followed a drifted P^{-1} into an ill-conditioned pivot
-        // block; keep the previous estimate and stop (reported as not converged)
+        // FP32 guard: a half-sweep whose estimate moves away from a plausible one by
+        // more than kBlowup times that one has followed a drifted P^{-1} into an
+        // ill-conditioned pivot block; keep the previous estimate and stop
         if constexpr (sizeof(R) == 4) {
-          if (change > kBlowup * sqrt(prev.x * prev.x + prev.y * prev.y)) {
-            est = prev;
-            if (tid == 0) x.fail_step = 7;
+          if (prev_ok && change > kBlowup * sqrt(prev.x * prev.x + prev.y * prev.y)) {
+            if (tid == 0) {
+              ss.est = prev;
+              x.fail_step = 7;
+            }
             break;
           }
         }
       }
-      prev = est;
+      if (tid == 0) {
+        ss.hist[s & 1] = est;
+        ss.ok_hist[s & 1] = est_ok;
+      }
     }
     if (tid == 0) {
+      double2 est = ss.est;
+      if constexpr (sizeof(R) == 4) {
+        if ((status == ST_OK || status == ST_NOT_CONVERGED) && !plausible(ss, est)) {
+          if (ss.have_trusted) {  // the latest plausible estimate
+            est = ss.trusted;
+            status = ST_NOT_CONVERGED;
+            x.fail_step = 7;
+          } else if (hypot(est.x, est.y) > ss.bound) {  // nothing reportable
+            status = ST_NUMERIC;
+            x.fail_step = 8;
+          }
+        }
+      }
       JobResult r;
       r.est_re = est.x;
       r.est_im = est.y;
-      r.norm_sum = norm_sum;
+      r.norm_sum = ss.norm_sum;
       r.flops = x.flops;
       r.evaluations = x.evals;
       r.swaps = x.swaps;
@@ -250,7 +317,7 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
   r.half_sweeps = 0;
   r.max_rank = 0;
   r.terms = count[i];
-  int worst_err = 0, worst_warn = 0;
+  int worst_err = 0, worst_warn = 0, err_step = 0;
   if (hstatus[i] < 0) worst_err = hstatus[i];
   for (int t = 0; t < count[i]; ++t) {
     const int j = first[i] + t;
@@ -267,10 +334,14 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
     if (q.fail_step != 0 && r.fail_step == 0) r.fail_step = q.fail_step;
     r.half_sweeps = max(r.half_sweeps, q.half_sweeps);
     r.max_rank = max(r.max_rank, q.max_rank);
-    if (q.status < 0 && (worst_err == 0 || q.status < worst_err)) worst_err = q.status;
+    if (q.status < 0 && (worst_err == 0 || q.status < worst_err)) {
+      worst_err = q.status;
+      err_step = q.fail_step;
+    }
     if (q.status > worst_warn) worst_warn = q.status;
   }
   r.status = worst_err != 0 ? worst_err : worst_warn;
+  if (worst_err != 0 && err_step != 0) r.fail_step = err_step;  // the failing train's step
   if (r.status < 0 || !isfinite(r.price)) {
     if (r.status >= 0) r.status = ST_NUMERIC;
     r.price = nan("");
@@ -617,6 +688,8 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
     const int N = p.n_grid;
     const double eta = 2.0 * p.trunc_L / N;
     const double weight = std::exp(-p.rate * T) * std::pow(eta / (2.0 * M_PI), d);
+    double cap = 0.0;  // a call on the minimum or maximum is worth less than the sum of the spots
+    for (int j = 0; j < d; ++j) cap += p.spot[j];
     std::vector<double> m(d);
     for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
     const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
@@ -633,6 +706,7 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
       jd.T = T;
       jd.L = p.trunc_L;
       jd.weight = weight;
+      jd.cap = cap;
       double* cv = params + poff;
       double* dl = cv + (size_t)d * d;
       double* pc = dl + d;
@@ -1092,6 +1166,8 @@ int prepare_static(tt_pricer* h, const tt_problem* probs, int count) {
     const int N = p.n_grid;
     const double eta = 2.0 * p.trunc_L / N;
     const double weight = std::exp(-p.rate * T) * std::pow(eta / (2.0 * M_PI), d);
+    double cap = 0.0;  // a call on the minimum or maximum is worth less than the sum of the spots
+    for (int j = 0; j < d; ++j) cap += p.spot[j];
     double m[TT_STATIC_MAX_D];
     for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
     const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
@@ -1108,6 +1184,7 @@ int prepare_static(tt_pricer* h, const tt_problem* probs, int count) {
       jd.T = T;
       jd.L = p.trunc_L;
       jd.weight = weight;
+      jd.cap = cap;
       double* cv = params + poff;
       double* dl = cv + (size_t)d * d;
       double* pc = dl + d;

@@ -443,70 +443,75 @@ __device__ __forceinline__ void minv_set(Ctx<R>& x, int kp, int t, int s, cpx<R>
 }
 
 // ---------------------------------------------------------------------------
-// M = P^{-1} by Gauss-Jordan with partial pivoting, in R, scratch in sw.
+// M = P^{-1} by Gauss-Jordan with partial pivoting on [P | I], in R, scratch in
+// sw.  Rows are never moved: the pivot of column c is the unused row with the
+// largest |entry|^2 (order[c]); every other row subtracts its multiple of the
+// pivot row at the columns right of c, and the threads holding column c + 1
+// collect its argmax, so a step costs one block barrier.  At the end row c of
+// P^{-1} is the right half of row order[c] over its pivot.
 // Returns false (M not written) when a pivot is zero or not finite.
 // ---------------------------------------------------------------------------
 template <typename R, bool TC>
 __device__ bool invert_pivots(Ctx<R>& x, int rho) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int w2 = 2 * rho, ld = w2 + 1;  // odd row stride: column accesses are conflict-free
   cpx<R>* G = x.sw;
+  int* order = x.selr;
   for (int idx = tid; idx < rho * rho; idx += kThreads) {
     const int r = idx / rho, c = idx % rho;
     G[r * ld + c] = x.P[r * x.rall + c];
     G[r * ld + rho + c] = cpx<R>{R(r == c), R(0)};
   }
-  if (tid == 0) x.misc[MISC_SING] = 0;
   __syncthreads();
-  for (int c = 0; c < rho; ++c) {
-    if (warp == 0) {
-      R v = R(-1);
-      int vi = INT_MAX;
-      for (int r = c + lane; r < rho; r += 32) am_merge(v, vi, cabs2(G[r * ld + c]), r);
-      warp_argmax(v, vi);
-      if (lane == 0) {
-        x.misc[MISC_PIV] = vi;
-        if (!(v > R(0)) || !(v < R(INFINITY))) x.misc[MISC_SING] = 1;
+  const int tpr = rho <= 32 ? 8 : 4;  // threads per row (rho <= 64)
+  const int myr = tid / tpr, part = tid % tpr;
+  R v = R(-1);
+  int vi = INT_MAX;
+  if (myr < rho && part == 0) am_merge(v, vi, cabs2(G[myr * ld]), myr);
+  int buf = 0;
+  block_argmax(v, vi, x.redv, x.redi, buf);
+  unsigned long long used = 0ull;
+  bool ok = true;
+  for (int c = 0; c < rho; ++c) {  // v, vi, used: block-uniform
+    if (!(v > R(0)) || !(v < R(INFINITY))) {
+      ok = false;
+      break;
+    }
+    const int p = vi;
+    if (tid == 0) order[c] = p;
+    used |= 1ull << p;
+    v = R(-1);
+    vi = INT_MAX;
+    if (myr < rho && myr != p) {
+      // column c and row p are only read in this step
+      const cpx<R> f = cmul(G[myr * ld + c], crecip(G[p * ld + c]));
+      for (int j = c + 1 + part; j < w2; j += tpr) {
+        cpx<R> a = G[myr * ld + j];
+        cfms(a, f, G[p * ld + j]);
+        G[myr * ld + j] = a;
+        if (j == c + 1 && j < rho && !((used >> myr) & 1ull)) am_merge(v, vi, cabs2(a), myr);
       }
     }
-    __syncthreads();
-    if (x.misc[MISC_SING]) break;  // block-uniform
-    const int p = x.misc[MISC_PIV];
-    if (p != c && p < rho) {
-      for (int j = tid; j < w2; j += kThreads) {
-        const cpx<R> t = G[c * ld + j];
-        G[c * ld + j] = G[p * ld + j];
-        G[p * ld + j] = t;
-      }
-    }
-    __syncthreads();
-    const cpx<R> inv = crecip(G[c * ld + c]);
-    for (int r = tid; r < rho; r += kThreads) x.swcol[r] = G[r * ld + c];
-    for (int j = tid; j < w2; j += kThreads) x.swrow[j] = cmul(G[c * ld + j], inv);
-    __syncthreads();
-    for (int idx = tid; idx < rho * w2; idx += kThreads) {
-      const int r = idx / w2, j = idx % w2;
-      if (r == c) {
-        G[r * ld + j] = x.swrow[j];
-      } else {
-        cfms(G[r * ld + j], x.swcol[r], x.swrow[j]);
-      }
-    }
-    __syncthreads();
+    buf ^= 1;
+    block_argmax(v, vi, x.redv, x.redi, buf);  // its barrier also publishes the updates
   }
-  const bool ok = !x.misc[MISC_SING];
   if (ok) {
     if constexpr (TC) {
       // the tensor-core operand: hi and lo K-major planes, zero outside rho x rho
       const int kp = tc::pad16(rho);
       for (int idx = tid; idx < kp * kp; idx += kThreads) {
         const int r = idx / kp, c = idx % kp;
-        minv_set(x, kp, r, c, (r < rho && c < rho) ? G[r * ld + rho + c] : cpx<R>{R(0), R(0)});
+        cpx<R> m = {R(0), R(0)};
+        if (r < rho && c < rho) {
+          const int pr = order[r];
+          m = cmul(G[pr * ld + rho + c], crecip(G[pr * ld + r]));
+        }
+        minv_set(x, kp, r, c, m);
       }
     } else {
       for (int idx = tid; idx < rho * rho; idx += kThreads) {
-        const int r = idx / rho, c = idx % rho;
-        x.M[r * x.rall + c] = G[r * ld + rho + c];
+        const int r = idx / rho, c = idx % rho, pr = order[r];
+        x.M[r * x.rall + c] = cmul(G[pr * ld + rho + c], crecip(G[pr * ld + r]));
       }
     }
   }

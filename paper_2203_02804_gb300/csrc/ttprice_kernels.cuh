@@ -133,6 +133,7 @@ struct JobDesc {
   unsigned long long seed;
   double T, D0, L;
   double logscale, sign, weight;  // true integrand = sign*exp(logscale + sum norms)*value
+  double cap;  // no-arbitrage bound on the train's share of the price: the sum of the spots
 };
 
 struct JobResult {

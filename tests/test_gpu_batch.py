@@ -93,3 +93,25 @@ def test_heterogeneous_subset_fp64(tp, batch):
         assert dg.status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
         ref, _, _ = ttcross.tt_price(p)
         assert math.isfinite(v) and abs(v / ref - 1) < 1e-6
+
+
+@pytest.mark.parametrize("engine", ["cuda", "tc"])
+def test_mixed_estimate_guard(tp, batch, engine):
+    """The mixed path's estimate checks on the hardest draws (max-calls with d >= 8
+    at rank 32, where FP32 half-sweeps can amplify rounding), stopped after 1 to 3
+    half-sweeps: a price reported as OK or not converged is a plausible one, in
+    (0, sum of spots] with an imaginary part at most 1/4 of it (every train's
+    share is checked that way, and the shares are positive); otherwise the
+    problem is a numeric error saying that no half-sweep estimate was plausible."""
+    idx = [i for i, p in enumerate(batch) if p.payoff == "max" and p.d >= 8 and p.max_rank == 32][:48]
+    sub = [batch[i] for i in idx]
+    for hs in (1, 2, 3):
+        pr = tp.Pricer(max_d=10, max_n=256, max_rank=32, max_batch=len(sub), precision="mixed",
+                       engine=engine, max_half_sweeps=hs)
+        rc, prices, diags = pr.evaluate(sub)
+        pr.close()
+        for p, v, dg in zip(sub, prices, diags):
+            if dg.status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED):
+                assert 0 < v <= float(np.sum(p.spot)) and abs(dg.imag_part) <= 0.25 * v, (hs, v, dg)
+            else:
+                assert dg.status == tp.TT_ERR_NUMERIC and dg.fail_step == 8, (hs, dg)
