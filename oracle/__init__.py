@@ -20,6 +20,9 @@ Modules
                    contract it with the quadrature weights (Section IV)
   splitmix      -- the SplitMix64 counter-based generator (Steele, Lea and
                    Flood 2014) used to draw the random initial pivots
+  twomps        -- the paper's two-train (bra-ket) form: the payoff transform
+                   and the characteristic function put into tensor-train form
+                   separately, then contracted site by site (Eq. braket)
   mlp           -- the learned surrogate's network in FP64: fully connected
                    layers with SiLU, their backward pass, MSE and Adam
                    (Kingma and Ba 2015); no counterpart in the paper

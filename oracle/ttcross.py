@@ -72,6 +72,7 @@ class CrossDiag:
     maxvol_unconverged: int = 0
     history: list = field(default_factory=list)
     ranks: list = field(default_factory=list)
+    train: list = None  # with keep_train: the cores of the latest left-to-right half-sweep
 
 
 # ----------------------------------------------------------------------------
@@ -336,7 +337,8 @@ def column_scaled(a_mat):
 
 
 def core_select(tensor, d, n, k, outer, cols, direction, opts, diag):
-    """Select rows of core k's fiber; returns (new index set, summed interpolant)."""
+    """Select rows of core k's fiber; returns (new index set, summed interpolant,
+    interpolation core G = A_c A_c[W]^{-1} as an (outer, N, rank) array)."""
     raw = _fiber(tensor, d, n, k, outer, cols, direction)
     diag.evaluations += raw.size
     a_mat = column_scaled(raw)
@@ -351,18 +353,22 @@ def core_select(tensor, d, n, k, outer, cols, direction, opts, diag):
     diag.swaps += swaps
     diag.maxvol_unconverged += 0 if ok else 1
     g = a_cols @ np.linalg.inv(a_cols[rows, :])
-    gsum = g.reshape(len(outer), n, len(rows)).sum(axis=1)
+    core = g.reshape(len(outer), n, len(rows))
+    gsum = core.sum(axis=1)
     if direction == "lr":
         new_set = [tuple(outer[w // n]) + (w % n,) for w in rows]
     else:
         new_set = [(w % n,) + tuple(outer[w // n]) for w in rows]
-    return new_set, gsum
+    return new_set, gsum, core
 
 
-def core_sum(tensor, d, n, k, outer, direction, diag):
-    """End core of a half-sweep: sum over its grid index, one value per outer index."""
+def core_sum(tensor, d, n, k, outer, direction, diag, end_core=None):
+    """End core of a half-sweep: sum over its grid index, one value per outer index
+    (the fiber itself, (outer, N, 1), is appended to ``end_core`` when given)."""
     a_mat = _fiber(tensor, d, n, k, outer, [()], direction)
     diag.evaluations += a_mat.size
+    if end_core is not None:
+        end_core.append(a_mat.reshape(len(outer), n, 1))
     return a_mat.reshape(len(outer), n).sum(axis=1)
 
 
@@ -370,8 +376,13 @@ def core_sum(tensor, d, n, k, outer, direction, diag):
 # the sweeps
 # ----------------------------------------------------------------------------
 
-def tt_cross_sum(tensor, r_max, seed, term=0, opts=None):
-    """TT-cross approximation of sum over the grid of ``tensor``; returns (sum, diag)."""
+def tt_cross_sum(tensor, r_max, seed, term=0, opts=None, keep_train=False):
+    """TT-cross approximation of sum over the grid of ``tensor``; returns (sum, diag).
+
+    With ``keep_train`` the cores of the latest left-to-right half-sweep are kept
+    in ``diag.train``: G_0, ..., G_{d-2} (interpolation cores, (r_{k-1}, N, r_k))
+    and the end core's fiber (r_{d-2}, N, 1); their product is the train whose
+    weighted sum that half-sweep estimated."""
     opts = opts or CrossOptions()
     d, n = tensor.d, tensor.n
     ranks = bond_ranks(d, n, r_max)
@@ -388,14 +399,18 @@ def tt_cross_sum(tensor, r_max, seed, term=0, opts=None):
     for s in range(opts.max_half_sweeps):
         if s % 2 == 0:
             v = np.ones(1, dtype=np.complex128)
+            cores = []
             for k in range(d - 1):
-                lsets[k + 1], gsum = core_select(tensor, d, n, k, lsets[k], rsets[k + 1], "lr", opts, diag)
+                lsets[k + 1], gsum, core = core_select(tensor, d, n, k, lsets[k], rsets[k + 1], "lr", opts, diag)
+                cores.append(core)
                 v = v @ gsum
-            est = complex(v @ core_sum(tensor, d, n, d - 1, lsets[d - 1], "lr", diag))
+            est = complex(v @ core_sum(tensor, d, n, d - 1, lsets[d - 1], "lr", diag, cores))
+            if keep_train:
+                diag.train = cores
         else:
             v = np.ones(1, dtype=np.complex128)
             for k in range(d - 1, 0, -1):
-                rsets[k], gsum = core_select(tensor, d, n, k, rsets[k + 1], lsets[k], "rl", opts, diag)
+                rsets[k], gsum, _ = core_select(tensor, d, n, k, rsets[k + 1], lsets[k], "rl", opts, diag)
                 v = gsum.T @ v
             est = complex(core_sum(tensor, d, n, 0, rsets[1], "rl", diag) @ v)
         diag.half_sweeps = s + 1
