@@ -58,6 +58,17 @@ typedef enum { TT_FP64 = 0, TT_MIXED = 1 } tt_precision;
    Results agree to the mixed path's tolerance; speed depends on the rank. */
 typedef enum { TT_ENGINE_AUTO = 0, TT_ENGINE_CUDA_CORES = 1, TT_ENGINE_TENSOR_CORES = 2 } tt_engine;
 
+/* TT_METHOD_SINGLE_TRAIN: TT-cross of the product integrand phi_T(-z) vhat(z), its
+ * train contracted with the weights.  TT_METHOD_TWO_TRAINS: the paper's bra-ket
+ * form (Section IV, Eq. braket): the payoff transform vhat(z) and the
+ * characteristic function phi_T(-z) are put into tensor-train form separately
+ * (same rank cap; a fixed max_half_sweeps, default 3: left-to-right,
+ * right-to-left, left-to-right, the train being the last one's cores; no
+ * sum-based stop) and the two trains are contracted site by site,
+ * E <- sum_i G^v_k(i)^T E G^phi_k(i), in FP64 in both precisions (TT_MIXED
+ * runs the two crosses in FP32).  Needs max_rank <= 32 and max_n <= 1024. */
+typedef enum { TT_METHOD_SINGLE_TRAIN = 0, TT_METHOD_TWO_TRAINS = 1 } tt_method;
+
 typedef struct {
   int max_d;            /* largest number of assets                        (1..255)  */
   int max_n;            /* largest grid size N per axis                    (2..4096) */
@@ -84,6 +95,7 @@ typedef struct {
                            once per batch layout on a stream the pricer owns and
                            ordered after / before cuda_stream by events; 0: plain
                            launches on cuda_stream                               */
+  int method;           /* tt_method (0: single train)                             */
   int device;           /* CUDA device ordinal                                     */
   void* cuda_stream;    /* cudaStream_t to run on; NULL = legacy default stream    */
   void* workspace;      /* optional device buffer of tt_workspace_bytes() bytes,
@@ -113,7 +125,8 @@ typedef struct {
   int status;            /* tt_status of this problem                              */
   int half_sweeps;       /* largest number of half-sweeps over its trains          */
   int final_rank_max;    /* largest TT rank after rank reduction                   */
-  int terms;             /* trains summed: 1 (min-call) or d (max-call)            */
+  int terms;             /* trains: 1 (min-call) or d (max-call), twice that in
+                            the two-train form (a vhat and a phi train per term)  */
   long long evaluations; /* integrand evaluations, fiber entries counted once      */
   long long maxvol_swaps; /* row swaps made by maxvol, all cores and half-sweeps    */
   long long block_visits; /* maxvol block visits (one block product B = A P^{-1} each) */
@@ -123,7 +136,9 @@ typedef struct {
                             6 a tensor-core block product did not complete (mixed);
                             8 (mixed) no half-sweep estimate of a train was
                             plausible (see 7) and the last one's share of the
-                            price exceeds the sum of the spots;
+                            price exceeds the sum of the spots; 9 (two-train
+                            form) a singular pivot block or a non-finite value
+                            in the bracket;
                             with TT_WARN_NOT_CONVERGED: 7 the mixed path reports an
                             earlier half-sweep's estimate of some train: the last one
                             moved by over 100x a plausible one before it, or was not

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
                                                             const int* __restrict__ order, int njobs,
                                                             int* counter, JobResult* results,
                                                             char* scratch, Layout lay, SmemLayout sl,
-                                                            Knobs kn) {
+                                                            Knobs kn, char* emit, size_t emit_stride) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double dscr[32];
   __shared__ SweepState ss;
@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       x.rmax = jd.rmax;
       x.cauchy = jd.cauchy;
       x.D0 = (R)jd.D0;
-      x.T = jd.T;
+      x.T = jd.Tq;
+      x.emit = jd.factor != FACTOR_PRODUCT ? emit + (size_t)jid * emit_stride : nullptr;
       x.cov = prm;
       x.flops = 0.0;
       x.evals = 0;
@@ -206,6 +207,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
         status = ST_NUMERIC;
         break;
       }
+      // A factor train of the two-train form runs a fixed count of half-sweeps: its
+      // own grid sum (the payoff transform's cancels to ~1e-10 of its entries) is no
+      // stop criterion and no share of the price.
+      if (x.emit) {
+        if (tid == 0) ss.est = est;
+        if (d == 1 || s + 1 == kn.max_half_sweeps) status = ST_OK;
+        continue;
+      }
       // The midpoint grid is symmetric and the payoff real, so the exact grid sum
       // is real and |Im est| is a lower bound on the estimate's error; the train's
       // share of the price lies in (0, sum of spots].  In FP32 a half-sweep built on
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
     if (tid == 0) {
       double2 est = ss.est;
       if constexpr (sizeof(R) == 4) {
-        if ((status == ST_OK || status == ST_NOT_CONVERGED) && !plausible(ss, est)) {
+        if ((status == ST_OK || status == ST_NOT_CONVERGED) && !x.emit && !plausible(ss, est)) {
           if (ss.have_trusted) {  // the latest plausible estimate
             est = ss.trusted;
             status = ST_NOT_CONVERGED;
@@ -323,9 +332,11 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
     const int j = first[i] + t;
     const JobDesc& jd = jobs[j];
     const JobResult& q = jres[j];
-    const double sc = jd.weight * jd.sign * exp(jd.logscale + q.norm_sum);
-    r.price += sc * q.est_re;
-    r.imag += sc * q.est_im;
+    if (jd.factor != FACTOR_PHI) {  // a payoff-transform train carries its bracket's value
+      const double sc = jd.weight * jd.sign * exp(jd.logscale + q.norm_sum);
+      r.price += sc * q.est_re;
+      r.imag += sc * q.est_im;
+    }
     r.flops += q.flops;
     r.evaluations += q.evaluations;
     r.swaps += q.swaps;
@@ -347,6 +358,295 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
     r.price = nan("");
   }
   out[i] = r;
+}
+
+// ---------------------------------------------------------------------------
+// Two-train form (Section IV, Eq. braket): the bracket <vhat | phi> of the two
+// factor trains of one term, contracted site by site, one CTA per bracket.
+// Each factor's cores are rebuilt from its skeleton (selected rows W_k, kept
+// columns K_k) with the cross's own integrand evaluation and column shifts:
+//   A_k(i) = F(I_{k-1}, i, K_k),  P_k = A_k[W_k],  G_k(i) = A_k(i) P_k^{-1}
+// (the shifts cancel in G), the end core G(i) = F(I_{d-2}, i); then
+//   E <- sum_i G^v_k(i)^T E G^phi_k(i),  E_0 = [1].
+// P_k^{-1} comes from FP64 Gauss-Jordan with partial pivoting; G and the
+// contraction run in R.  The bracket, in the v train's normalised units, goes
+// to that train's result; the phi train's carries no price.
+// ---------------------------------------------------------------------------
+struct BrSmem {
+  int tab[2], cshift[2], cref[2], lsz[2], rsz[2], W[2];
+  int E, X, Av, Af, Gv, Gf, Mv, Mf, red, total;
+};
+
+// FP64 [P | I] -> P^{-1} (n x n, rows of length ld >= 2n in G), written to M in R
+// (leading dimension n); false when a pivot is zero or not finite.
+template <typename R>
+__device__ bool gj_inverse_f64(double2* G, int n, int ld, cpx<R>* M, double* redv, int* redi) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int c = 0; c < n; ++c) {
+    if (warp == 0) {
+      double v = -1.0;
+      int vi = INT_MAX;
+      for (int r = c + lane; r < n; r += 32) {
+        const double2 g = G[r * ld + c];
+        am_merge(v, vi, g.x * g.x + g.y * g.y, r);
+      }
+      warp_argmax(v, vi);
+      if (lane == 0) {
+        redv[0] = v;
+        redi[0] = vi;
+      }
+    }
+    __syncthreads();
+    const double pv = redv[0];
+    const int p = redi[0];
+    if (!(pv > 0.0) || !(pv < 1e300)) return false;  // block-uniform
+    if (p != c)
+      for (int j = tid; j < 2 * n; j += kThreads) {
+        const double2 a = G[c * ld + j];
+        G[c * ld + j] = G[p * ld + j];
+        G[p * ld + j] = a;
+      }
+    __syncthreads();
+    const double2 g = G[c * ld + c];
+    const double2 inv = make_double2(g.x / pv, -g.y / pv);
+    __syncthreads();  // every thread has read the pivot before row c is scaled
+    for (int j = c + tid; j < 2 * n; j += kThreads) {
+      const double2 a = G[c * ld + j];
+      G[c * ld + j] = make_double2(a.x * inv.x - a.y * inv.y, a.x * inv.y + a.y * inv.x);
+    }
+    __syncthreads();
+    const int w = 2 * n - c - 1;  // columns right of c
+    for (int idx = tid; idx < n * w; idx += kThreads) {
+      const int r = idx / w, j = c + 1 + idx % w;
+      if (r == c) continue;
+      const double2 f = G[r * ld + c], b = G[c * ld + j];
+      double2 a = G[r * ld + j];
+      a.x -= f.x * b.x - f.y * b.y;
+      a.y -= f.x * b.y + f.y * b.x;
+      G[r * ld + j] = a;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < n * n; idx += kThreads) {
+    const int r = idx / n, c = idx % n;
+    const double2 a = G[r * ld + n + c];
+    M[idx] = cpx<R>{(R)a.x, (R)a.y};
+  }
+  __syncthreads();
+  return true;
+}
+
+template <typename R>
+__device__ void bracket_ctx(Ctx<R>& x, const JobDesc& jd, const double* params, char* base, const Layout& lay,
+                            unsigned char* smem, const BrSmem& S, int f, int* misc) {
+  x.dmax = lay.dmax;
+  x.nmax = lay.nmax;
+  x.rall = lay.rmax;
+  x.d = jd.d;
+  x.n = jd.n;
+  x.rmax = jd.rmax;
+  x.cauchy = jd.cauchy;
+  x.D0 = (R)jd.D0;
+  x.T = jd.Tq;
+  x.cov = params + jd.param_off;
+  x.u = reinterpret_cast<double*>(base + lay.u);
+  x.lam = reinterpret_cast<double*>(base + lay.lam);
+  x.om = reinterpret_cast<double2*>(base + lay.om);
+  x.lset = reinterpret_cast<uint16_t*>(base + lay.lset);
+  x.rset = reinterpret_cast<uint16_t*>(base + lay.rset);
+  x.lstate = reinterpret_cast<double*>(base + lay.lstate);
+  x.rstate = reinterpret_cast<double*>(base + lay.rstate);
+  x.lvec = reinterpret_cast<double*>(base + lay.lvec);
+  x.rvec = reinterpret_cast<double*>(base + lay.rvec);
+  x.pair = reinterpret_cast<PairE<R>*>(base + lay.pair);
+  R* tab = reinterpret_cast<R*>(smem + S.tab[f]);
+  x.tl = tab;
+  x.tu = tab + lay.nmax;
+  x.tor = tab + 2 * lay.nmax;
+  x.toi = tab + 3 * lay.nmax;
+  x.cshift = reinterpret_cast<R*>(smem + S.cshift[f]);
+  x.cref = reinterpret_cast<R*>(smem + S.cref[f]);
+  x.lsz = reinterpret_cast<int*>(smem + S.lsz[f]);
+  x.rsz = reinterpret_cast<int*>(smem + S.rsz[f]);
+  x.stage = nullptr;
+  x.stage_lo = 0;
+  x.stage_n = 0;
+  x.misc = misc;
+  x.flops = 0.0;
+  x.evals = 0;
+  x.emit = nullptr;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 1) bracket_kernel(const JobDesc* __restrict__ jobs,
+                                                              const double* __restrict__ params,
+                                                              const int2* __restrict__ pairs, int npairs,
+                                                              const char* __restrict__ emit, size_t emit_stride,
+                                                              JobResult* results, char* scratch, Layout lay,
+                                                              BrSmem S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double dscr[32];
+  __shared__ Ctx<R> xs[2];
+  __shared__ int misc[16];
+  const int tid = threadIdx.x;
+  const size_t ecb = emit_core_bytes(lay.rmax, lay.dmax);
+  cpx<R>* E = reinterpret_cast<cpx<R>*>(smem + S.E);
+  cpx<R>* X = reinterpret_cast<cpx<R>*>(smem + S.X);
+  cpx<R>* Av = reinterpret_cast<cpx<R>*>(smem + S.Av);
+  cpx<R>* Af = reinterpret_cast<cpx<R>*>(smem + S.Af);
+  cpx<R>* Gv = reinterpret_cast<cpx<R>*>(smem + S.Gv);
+  cpx<R>* Gf = reinterpret_cast<cpx<R>*>(smem + S.Gf);
+  double* redv = reinterpret_cast<double*>(smem + S.red);
+  int* redi = reinterpret_cast<int*>(redv + 2);
+  constexpr int kAcc = 4;  // accumulator entries per thread: rank <= 32 on both trains
+  for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+    const int2 jp = pairs[pr];
+    const JobDesc jv = jobs[jp.x], jf = jobs[jp.y];
+    if (results[jp.x].status < 0 || results[jp.y].status < 0) continue;  // a train failed: the price is NaN
+    if (tid == 0) {
+      for (int f = 0; f < 2; ++f)
+        bracket_ctx(xs[f], f ? jf : jv, params, scratch + (2 * (size_t)blockIdx.x + f) * lay.stride, lay, smem, S,
+                    f, misc);
+    }
+    __syncthreads();
+    double ns[2];
+    for (int f = 0; f < 2; ++f) job_setup(xs[f], f ? jf : jv, params + (f ? jf : jv).param_off, dscr, ns[f], false);
+    const int d = jv.d, N = jv.n;
+    if (tid == 0) E[0] = cpx<R>{R(1), R(0)};
+    bool ok = true;
+    double lu = 0.0;
+    for (int k = 0; k < d && ok; ++k) {
+      const bool last = k == d - 1;
+      for (int f = 0; f < 2 && ok; ++f) {
+        Ctx<R>& x = xs[f];
+        int* W = reinterpret_cast<int*>(smem + S.W[f]);
+        const char* e = emit + (size_t)(f ? jp.y : jp.x) * emit_stride + (size_t)k * ecb;
+        const int rp = x.lsz[k];
+        const int rk = last ? 1 : *reinterpret_cast<const int*>(e);
+        if (!last) {
+          const int* ew = reinterpret_cast<const int*>(e) + 1;
+          const uint16_t* ek = reinterpret_cast<const uint16_t*>(ew + lay.rmax);
+          const int wr = d - k - 1;
+          for (int idx = tid; idx < rk * wr; idx += kThreads) {
+            const int t = idx / wr, pos = idx % wr;
+            rset_at(x, k + 1, t)[pos] = ek[t * lay.dmax + pos];
+          }
+          for (int t = tid; t < rk; t += kThreads) W[t] = ew[t];
+          if (tid == 0) x.rsz[k + 1] = rk;
+        }
+        __syncthreads();
+        core_states(x, k, DIR_LR);
+        load_axis_table(x, k);
+        column_shifts(x, rp, rk);
+        if (!last) {
+          // the pivot block A[W, :] in FP64, inverted
+          double2* G = reinterpret_cast<double2*>(smem + S.X);
+          const int ld = 2 * rk;
+          for (int idx = tid; idx < rk * rk; idx += kThreads) {
+            const int t = idx / rk, c = idx % rk, g = W[t];
+            const cpx<R> a = eval_point(x, g / N, g % N, c);
+            G[t * ld + c] = make_double2((double)a.re, (double)a.im);
+            G[t * ld + rk + c] = make_double2(t == c ? 1.0 : 0.0, 0.0);
+          }
+          __syncthreads();
+          ok = gj_inverse_f64(G, rk, ld, reinterpret_cast<cpx<R>*>(smem + (f ? S.Mf : S.Mv)), redv, redi);
+        } else if (tid == 0) {
+          lu += Num<R>::log_unscale((double)x.cshift[0]);
+        }
+      }
+      if (!ok) break;
+      const int rpv = xs[0].lsz[k], rkv = last ? 1 : xs[0].rsz[k + 1];
+      const int rpf = xs[1].lsz[k], rkf = last ? 1 : xs[1].rsz[k + 1];
+      const cpx<R>* Mv = reinterpret_cast<const cpx<R>*>(smem + S.Mv);
+      const cpx<R>* Mf = reinterpret_cast<const cpx<R>*>(smem + S.Mf);
+      cpx<R> acc[kAcc];
+#pragma unroll
+      for (int q = 0; q < kAcc; ++q) acc[q] = cpx<R>{R(0), R(0)};
+      for (int i = 0; i < N; ++i) {
+        for (int idx = tid; idx < rpv * rkv; idx += kThreads) Av[idx] = eval_point(xs[0], idx / rkv, i, idx % rkv);
+        for (int idx = tid; idx < rpf * rkf; idx += kThreads) Af[idx] = eval_point(xs[1], idx / rkf, i, idx % rkf);
+        __syncthreads();
+        const cpx<R>* gv = Av;
+        const cpx<R>* gf = Af;
+        if (!last) {  // G(i) = A(i) P^{-1}
+          for (int idx = tid; idx < rpv * rkv; idx += kThreads) {
+            const int a = idx / rkv, t = idx % rkv;
+            cpx<R> s2 = {R(0), R(0)};
+            for (int c = 0; c < rkv; ++c) cfma(s2, Av[a * rkv + c], Mv[c * rkv + t]);
+            Gv[idx] = s2;
+          }
+          for (int idx = tid; idx < rpf * rkf; idx += kThreads) {
+            const int b = idx / rkf, t = idx % rkf;
+            cpx<R> s2 = {R(0), R(0)};
+            for (int c = 0; c < rkf; ++c) cfma(s2, Af[b * rkf + c], Mf[c * rkf + t]);
+            Gf[idx] = s2;
+          }
+          __syncthreads();
+          gv = Gv;
+          gf = Gf;
+        }
+        // X = E G^phi(i): rpv x rkf
+        for (int idx = tid; idx < rpv * rkf; idx += kThreads) {
+          const int a = idx / rkf, t = idx % rkf;
+          cpx<R> s2 = {R(0), R(0)};
+          for (int b = 0; b < rpf; ++b) cfma(s2, E[a * rpf + b], gf[b * rkf + t]);
+          X[idx] = s2;
+        }
+        __syncthreads();
+        // acc(a', b') += sum_a G^v(i)[a][a'] X[a][b']
+#pragma unroll
+        for (int q = 0; q < kAcc; ++q) {
+          const int idx = tid + q * kThreads;
+          if (idx < rkv * rkf) {
+            const int ap = idx / rkf, bp = idx % rkf;
+            for (int a = 0; a < rpv; ++a) cfma(acc[q], gv[a * rkv + ap], X[a * rkf + bp]);
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < kAcc; ++q) {
+        const int idx = tid + q * kThreads;
+        if (idx < rkv * rkf) E[idx] = acc[q];
+      }
+      if (tid == 0) {
+        const double pts = (double)N * (rpv * rkv + rpf * rkf);
+        xs[0].evals += (long long)pts;
+        xs[0].flops += 24.0 * pts + 8.0 * N * ((last ? 0.0 : (double)rpv * rkv * rkv + (double)rpf * rkf * rkf) +
+                                               (double)rpv * rpf * rkf + (double)rpv * rkv * rkf);
+      }
+      // next core's left sets: I_k[t] = I_{k-1}[W[t] / N] followed by W[t] % N
+      if (!last) {
+        for (int f = 0; f < 2; ++f) {
+          Ctx<R>& x = xs[f];
+          const int* W = reinterpret_cast<const int*>(smem + S.W[f]);
+          const int rk = x.rsz[k + 1], w = k + 1;
+          for (int idx = tid; idx < rk * w; idx += kThreads) {
+            const int t = idx / w, pos = idx % w, g = W[t];
+            lset_at(x, k + 1, t)[pos] = pos < k ? lset_at(x, k, g / N)[pos] : (uint16_t)(g % N);
+          }
+          if (tid == 0) x.lsz[k + 1] = rk;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      JobResult r = results[jp.x];
+      const cpx<R> b = E[0];
+      if (ok && isfinite((double)b.re) && isfinite((double)b.im)) {
+        r.est_re = (double)b.re;
+        r.est_im = (double)b.im;
+        r.norm_sum = ns[0] + ns[1] + jf.logscale + lu;
+      } else {
+        r.status = ST_NUMERIC;
+        r.fail_step = 9;
+      }
+      r.flops += xs[0].flops;
+      r.evaluations += xs[0].evals;
+      results[jp.x] = r;
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace ttp
@@ -385,6 +685,9 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.block_rows < o.max_rank || o.block_rows + o.max_rank > ttp::kThreads) return false;
   if (o.engine < TT_ENGINE_AUTO || o.engine > TT_ENGINE_TENSOR_CORES) return false;
   if (o.graph != 0 && o.graph != 1) return false;
+  if (o.method != TT_METHOD_SINGLE_TRAIN && o.method != TT_METHOD_TWO_TRAINS) return false;
+  const bool two = o.method == TT_METHOD_TWO_TRAINS;
+  if (two && (o.max_rank > 32 || o.max_n > 1024)) return false;  // the bracket kernel's tile sizes
   if (o.precision == TT_FP64) {
     if (o.engine == TT_ENGINE_TENSOR_CORES) return false;  // no FP64 tensor-core product
     o.engine = TT_ENGINE_CUDA_CORES;
@@ -393,7 +696,7 @@ bool resolve(const tt_options* in, Resolved* r) {
   }
   // the tensor-core block product is one 128-row tile
   if (o.engine == TT_ENGINE_TENSOR_CORES && o.block_rows > ttp::tc::kRows) return false;
-  if (o.max_half_sweeps == 0) o.max_half_sweeps = 8;
+  if (o.max_half_sweeps == 0) o.max_half_sweeps = two ? 3 : 8;
   if (o.max_half_sweeps < 1 || o.max_half_sweeps > 1000) return false;
   const bool f64 = o.precision == TT_FP64;
   if (!(o.sweep_tol > 0)) o.sweep_tol = f64 ? 1e-6 : 1e-4;
@@ -406,7 +709,7 @@ bool resolve(const tt_options* in, Resolved* r) {
   r->kn.sweep_tol = o.sweep_tol;
   r->kn.max_half_sweeps = o.max_half_sweeps;
   r->kn.block_rows = o.block_rows;
-  const long long mj = (long long)o.max_batch * o.max_d;
+  const long long mj = (long long)o.max_batch * o.max_d * (two ? 2 : 1);
   if (mj > (1 << 24)) return false;
   r->max_jobs = (int)mj;
   r->max_params = (size_t)r->max_jobs * ((size_t)o.max_d * o.max_d + 3 * (size_t)o.max_d);
@@ -490,9 +793,42 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   return S;
 }
 
+// the bracket kernel's shared memory (two-train form)
+ttp::BrSmem make_brsmem(const tt_options& o, bool f64) {
+  ttp::BrSmem S;
+  const int rs = f64 ? 8 : 4, cs = 2 * rs;
+  const int r = o.max_rank, n = o.max_n, d = o.max_d;
+  int off = 0;
+  auto take = [&](int bytes) {
+    int at = off;
+    off = (int)align_up(off + bytes, 16);
+    return at;
+  };
+  for (int f = 0; f < 2; ++f) {
+    S.tab[f] = take(4 * n * rs);
+    S.cshift[f] = take((r + 1) * rs);
+    S.cref[f] = take((r + 1) * rs);
+    S.lsz[f] = take((d + 1) * 4);
+    S.rsz[f] = take((d + 1) * 4);
+    S.W[f] = take(r * 4);
+  }
+  S.E = take(r * r * cs);
+  // X .. Gf are contiguous: the FP64 Gauss-Jordan buffer [P | I] (r x 2r) aliases them
+  S.X = take(r * r * cs);
+  S.Av = take(r * r * cs);
+  S.Af = take(r * r * cs);
+  S.Gv = take(r * r * cs);
+  S.Gf = take(std::max(r * r * cs, 2 * r * r * 16 - (off - S.X)));
+  S.Mv = take(r * r * cs);
+  S.Mf = take(r * r * cs);
+  S.red = take(32);
+  S.total = off;
+  return S;
+}
+
 struct DevLayout {  // offsets inside the device workspace
-  size_t stage, stage_bytes, jres, ires, counter, scratch, total;
-  size_t o_jobs, o_params, o_order, o_first, o_count, o_hstatus;  // inside the stage block
+  size_t stage, stage_bytes, jres, ires, counter, scratch, emit, emit_stride, total;
+  size_t o_jobs, o_params, o_order, o_first, o_count, o_hstatus, o_pairs;  // inside the stage block
 };
 
 DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
@@ -510,6 +846,8 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   D.o_first = take(sizeof(int) * R.o.max_batch);
   D.o_count = take(sizeof(int) * R.o.max_batch);
   D.o_hstatus = take(sizeof(int) * R.o.max_batch);
+  const bool two = R.o.method == TT_METHOD_TWO_TRAINS;
+  D.o_pairs = take(two ? sizeof(int2) * (size_t)R.max_jobs / 2 : 0);
   D.stage_bytes = s;
   size_t off = 0;
   auto take2 = [&](size_t bytes) {
@@ -522,6 +860,9 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   D.ires = take2(sizeof(InstanceResult) * R.o.max_batch);
   D.counter = take2(sizeof(int) * 4);
   D.scratch = take2(L.stride * (size_t)grid);
+  // two-train form: every factor train's skeleton records, one per core
+  D.emit_stride = two ? align_up(ttp::emit_core_bytes(L.rmax, L.dmax) * L.dmax, A) : 0;
+  D.emit = take2(D.emit_stride * (two ? (size_t)R.max_jobs : 0));
   D.total = off;
   return D;
 }
@@ -618,8 +959,10 @@ struct tt_pricer {
   char* h_stage;           // pinned, capacity layout, filled by validation
   char* h_pack;            // pinned, packed copy that is sent to the device
   InstanceResult* h_ires;  // pinned
-  int count, njobs;
-  size_t p_jobs, p_params, p_order, p_first, p_count, p_hstatus, p_bytes;  // packed offsets
+  int count, njobs, npairs;
+  size_t p_jobs, p_params, p_order, p_first, p_count, p_hstatus, p_pairs, p_bytes;  // packed offsets
+  ttp::BrSmem bsm;  // two-train form: the bracket kernel's shared-memory carve
+  int bgrid;
   size_t last_h2d, last_d2h;
   // graph replay (options.graph): the capture stream, ordering events, the
   // instantiated graph and the batch layout it was captured for
@@ -641,7 +984,9 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   int* first = reinterpret_cast<int*>(st + h->dl.o_first);
   int* cnt = reinterpret_cast<int*>(st + h->dl.o_count);
   int* hstat = reinterpret_cast<int*>(st + h->dl.o_hstatus);
-  int nj = 0;
+  int2* pairs = reinterpret_cast<int2*>(st + h->dl.o_pairs);
+  const bool two = o.method == TT_METHOD_TWO_TRAINS;
+  int nj = 0, np = 0;
   size_t poff = 0;
   std::vector<double> cost;
   cost.reserve((size_t)count * 2);
@@ -693,6 +1038,95 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
     std::vector<double> m(d);
     for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
     const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
+    if (two) {
+      // Two-train form (Eq. braket): per term a payoff-transform train and a
+      // characteristic-function train, in the term's variables.  With mu_t the
+      // term's mean log-price vector, s the strike's direction (all ones for the
+      // min-call, e_j for max-call term j), delta the shift and C the covariance:
+      //   phi_T(-z) = exp(delta.mu_t + T/2 delta^T C delta) exp(-T/2 u^T C u)
+      //               * exp(-i u.(mu_t + T C delta)),
+      //   vhat(z)   = K^(1 - s.delta) e^{i ln K s.u} * (rational factors: 1/(i z_l),
+      //               1/((i z_j)(1 + i z_j)), and the min-call's 1/(1 + i sum z)).
+      const bool mn = p.payoff == TT_MIN_CALL;
+      std::vector<double> cvv((size_t)d * d), dlv(d), kdv(d), mut(d), sv(d), cd(d);
+      for (int term = 0; term < terms; ++term) {
+        const int j0 = term;
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) {
+            auto cov = [&](int r, int c) { return p.cov[r * d + c]; };
+            double v = cov(a, b);
+            if (!mn) {
+              if (a != j0) v -= cov(j0, b);
+              if (b != j0) v -= cov(a, j0);
+              if (a != j0 && b != j0) v += cov(j0, j0);
+            }
+            cvv[(size_t)a * d + b] = v;
+          }
+        for (int l = 0; l < d; ++l) {
+          if (mn) {
+            dlv[l] = -p.damping[l];
+            kdv[l] = 0.0;
+            mut[l] = m[l] + lk;
+            sv[l] = 1.0;
+          } else {
+            dlv[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
+            kdv[l] = l == j0 ? 1.0 : 0.0;
+            mut[l] = l == j0 ? m[j0] + lk : m[l] - m[j0];
+            sv[l] = l == j0 ? 1.0 : 0.0;
+          }
+        }
+        double quad = 0.0, sdl = 0.0, dmu = 0.0;
+        for (int l = 0; l < d; ++l) {
+          double c = 0.0;
+          for (int q = 0; q < d; ++q) c += cvv[(size_t)l * d + q] * dlv[q];
+          cd[l] = c;
+          quad += dlv[l] * c;
+          sdl += dlv[l] * sv[l];
+          dmu += dlv[l] * mut[l];
+        }
+        pairs[np].x = nj;
+        pairs[np].y = nj + 1;
+        ++np;
+        for (int fi = 0; fi < 2; ++fi) {
+          const bool vh = fi == 0;
+          JobDesc jd;
+          std::memset(&jd, 0, sizeof(jd));
+          jd.d = d;
+          jd.n = N;
+          jd.rmax = p.max_rank;
+          jd.instance = i;
+          jd.term = term;
+          jd.param_off = (int)poff;
+          jd.factor = vh ? ttp::FACTOR_VHAT : ttp::FACTOR_PHI;
+          jd.seed = p.seed;
+          jd.T = T;
+          jd.Tq = vh ? 0.0 : T;
+          jd.L = p.trunc_L;
+          jd.weight = weight;
+          jd.cap = cap;
+          double* cv = params + poff;
+          double* dl = cv + (size_t)d * d;
+          double* pc = dl + d;
+          double* kd = pc + d;
+          poff += (size_t)d * d + 3 * (size_t)d;
+          std::memcpy(cv, cvv.data(), sizeof(double) * d * d);
+          for (int l = 0; l < d; ++l) {
+            dl[l] = dlv[l];
+            pc[l] = vh ? -lk * sv[l] : mut[l] + T * cd[l];
+            kd[l] = vh ? kdv[l] : 2.0;
+          }
+          jd.cauchy = vh && mn ? 1 : 0;
+          jd.D0 = vh && mn ? 1.0 - sdl : 0.0;
+          jd.logscale = vh ? lk * (1.0 - sdl) : dmu + 0.5 * T * quad;
+          jd.sign = vh && mn && d % 2 == 0 ? -1.0 : 1.0;  // (-1)^(d+1) on the min-call's transform
+          jobs[nj] = jd;
+          cost.push_back((double)std::max(d - 1, 1) * N * (double)p.max_rank * p.max_rank * (d > 1 ? 1.0 : 0.01));
+          ++nj;
+          ++cnt[i];
+        }
+      }
+      continue;
+    }
     for (int term = 0; term < terms; ++term) {
       JobDesc jd;
       std::memset(&jd, 0, sizeof(jd));
@@ -704,6 +1138,7 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
       jd.param_off = (int)poff;
       jd.seed = p.seed;
       jd.T = T;
+      jd.Tq = T;
       jd.L = p.trunc_L;
       jd.weight = weight;
       jd.cap = cap;
@@ -771,6 +1206,7 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   std::stable_sort(order, order + nj, [&](int a, int b) { return cost[a] > cost[b]; });
   h->count = count;
   h->njobs = nj;
+  h->npairs = np;
   // pack the used parts into one contiguous block: one host-to-device copy
   size_t off = 0;
   auto put = [&](size_t src_off, size_t bytes) {
@@ -785,6 +1221,7 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   h->p_first = put(h->dl.o_first, sizeof(int) * count);
   h->p_count = put(h->dl.o_count, sizeof(int) * count);
   h->p_hstatus = put(h->dl.o_hstatus, sizeof(int) * count);
+  h->p_pairs = put(h->dl.o_pairs, sizeof(int2) * np);
   h->p_bytes = off;
   h->last_h2d = off;
   if (off && cudaMemcpyAsync(h->ws + h->dl.stage, h->h_pack, off, cudaMemcpyHostToDevice,
@@ -806,17 +1243,29 @@ int launch_all(tt_pricer* h, cudaStream_t stream) {
   InstanceResult* ires = reinterpret_cast<InstanceResult*>(h->ws + h->dl.ires);
   char* scratch = h->ws + h->dl.scratch;
   if (cudaMemsetAsync(counter, 0, sizeof(int), stream) != cudaSuccess) return TT_ERR_CUDA;
+  char* emit = h->ws + h->dl.emit;
+  const size_t es = h->dl.emit_stride;
   if (h->njobs > 0) {
     const int grid = std::min(h->grid, h->njobs);
     if (h->R.o.precision == TT_FP64)
       ttp::tt_cross_kernel<double, false><<<grid, ttp::kThreads, h->sml.total, stream>>>(
-          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es);
     else if (h->R.o.engine == TT_ENGINE_TENSOR_CORES)
       ttp::tt_cross_kernel<float, true><<<grid, ttp::kThreads, h->sml.total, stream>>>(
-          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es);
     else
       ttp::tt_cross_kernel<float, false><<<grid, ttp::kThreads, h->sml.total, stream>>>(
-          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn);
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es);
+    if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
+  }
+  if (h->npairs > 0) {  // two-train form: the brackets, two scratch blocks per CTA
+    const int2* pairs = reinterpret_cast<const int2*>(st + h->p_pairs);
+    const int bg = std::min(h->bgrid, h->npairs);
+    // FP64 in both paths: in the mixed path the FP32 crosses choose the index sets,
+    // and the cores G = A P^{-1} are formed from FP64 integrand values (P can be
+    // conditioned up to 1/rank_tol, which FP32 values would turn into 1e-3 errors)
+    ttp::bracket_kernel<double><<<bg, ttp::kThreads, h->bsm.total, stream>>>(
+        jobs, params, pairs, h->npairs, emit, es, jres, scratch, h->lay, h->bsm);
     if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
   }
   if (h->count > 0) {
@@ -832,7 +1281,7 @@ int launch_all(tt_pricer* h, cudaStream_t stream) {
 int run_impl(tt_pricer* h) {
   if (!h->R.o.graph) return launch_all(h, h->stream);
   const size_t key[8] = {(size_t)h->njobs, (size_t)h->count, h->p_jobs, h->p_params,
-                         h->p_order, h->p_first, h->p_count, h->p_hstatus};
+                         h->p_order, h->p_first, h->p_count, h->p_hstatus ^ (h->p_pairs << 32) ^ (size_t)h->npairs};
   if (!h->gexec || std::memcmp(key, h->gkey, sizeof(key)) != 0) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
@@ -908,7 +1357,7 @@ size_t tt_workspace_bytes(const tt_options* opt) {
   int grid = 0;
   if (cudaSetDevice(R.o.device) != cudaSuccess) return 0;
   if (grid_for(R.o, S, &grid) != TT_OK) return 0;
-  Layout L = make_layout(R.o, f64);
+  Layout L = make_layout(R.o, f64 || R.o.method == TT_METHOD_TWO_TRAINS);
   return make_dev_layout(R, L, grid).total;
 }
 
@@ -927,9 +1376,23 @@ int tt_price_create(const tt_options* opt, tt_pricer** out) {
   tt_pricer* h = new (std::nothrow) tt_pricer();
   if (!h) return TT_ERR_INVALID;
   h->R = R;
-  h->lay = make_layout(R.o, f64);
+  h->lay = make_layout(R.o, f64 || R.o.method == TT_METHOD_TWO_TRAINS);  // the bracket runs in FP64
   h->sml = S;
   h->grid = grid;
+  h->npairs = 0;
+  h->bgrid = 0;
+  h->bsm = ttp::BrSmem{};
+  if (R.o.method == TT_METHOD_TWO_TRAINS) {
+    h->bsm = make_brsmem(R.o, true);
+    const cudaError_t e = cudaFuncSetAttribute(ttp::bracket_kernel<double>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, h->bsm.total);
+    if (h->bsm.total > 227 * 1024 || e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return TT_ERR_CAPACITY;
+    }
+    h->bgrid = std::max(1, grid / 2);
+  }
   h->dl = make_dev_layout(R, h->lay, grid);
   h->stream = reinterpret_cast<cudaStream_t>(R.o.cuda_stream);
   h->count = 0;
@@ -952,7 +1415,7 @@ int tt_price_create(const tt_options* opt, tt_pricer** out) {
   h->h_stage = nullptr;
   h->h_pack = nullptr;
   h->h_ires = nullptr;
-  h->p_jobs = h->p_params = h->p_order = h->p_first = h->p_count = h->p_hstatus = h->p_bytes = 0;
+  h->p_jobs = h->p_params = h->p_order = h->p_first = h->p_count = h->p_hstatus = h->p_pairs = h->p_bytes = 0;
   h->last_h2d = h->last_d2h = 0;
   h->cap = nullptr;
   h->ev_in = h->ev_out = nullptr;
@@ -1182,6 +1645,7 @@ int prepare_static(tt_pricer* h, const tt_problem* probs, int count) {
       jd.param_off = (int)poff;
       jd.seed = p.seed;
       jd.T = T;
+      jd.Tq = T;
       jd.L = p.trunc_L;
       jd.weight = weight;
       jd.cap = cap;
@@ -1336,6 +1800,8 @@ extern "C" int tt_price_evaluate_static(const tt_problem* probs, int count, int 
   h.h_ires = g_static_ires;
   h.count = 0;
   h.njobs = 0;
+  h.npairs = 0;
+  h.p_pairs = 0;
   h.last_h2d = h.last_d2h = 0;
   rc = prepare_static(&h, probs, count);
   if (rc != TT_OK) return rc;

@@ -48,10 +48,12 @@ constexpr int kPeakAttempts = 64;
 // For axis j and grid point u the separable factor is
 //   kind 0:  1/(i u - delta_j)                       * e^{-i p_j u}
 //   kind 1:  1/((i u - delta_j)(1 - delta_j + i u))  * e^{-i p_j u}
+//   kind 2:  e^{-i p_j u}  (the characteristic function alone, two-train form)
 // stored as log|.| (minus its maximum over the grid) and a unit phase.
+// `draw` = false builds the tables only (no initial right sets).
 template <typename R>
 __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, double* dscr,
-                          double& norm_sum) {
+                          double& norm_sum, bool draw = true) {
   const int d = jd.d, n = jd.n, tid = threadIdx.x;
   const double* delta = prm + d * d;
   const double* pcoef = delta + d;
@@ -68,9 +70,12 @@ __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, doubl
       // modulo 2 pi in FP64; the bounded parts (log-magnitudes, the arguments of
       // the rational factors, the sine/cosine of the reduced angle) in FP32.
       const float uf = (float)u, df = (float)dl;
-      float lrf = -0.5f * logf(uf * uf + df * df);
-      float pr = -atan2f(uf, -df);
-      if (kind[j] != 0.0) {
+      float lrf = 0.0f, pr = 0.0f;
+      if (kind[j] != 2.0) {
+        lrf = -0.5f * logf(uf * uf + df * df);
+        pr = -atan2f(uf, -df);
+      }
+      if (kind[j] == 1.0) {
         const float ef = 1.0f - df;
         lrf += -0.5f * logf(uf * uf + ef * ef);
         pr -= atan2f(uf, ef);
@@ -84,9 +89,13 @@ __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, doubl
       c = cf;
       s = sf;
     } else {
-      lr = -0.5 * log(u * u + dl * dl);
-      double ph = -pcoef[j] * u - atan2(u, -dl);
-      if (kind[j] != 0.0) {
+      lr = 0.0;
+      double ph = -pcoef[j] * u;
+      if (kind[j] != 2.0) {
+        lr = -0.5 * log(u * u + dl * dl);
+        ph -= atan2(u, -dl);
+      }
+      if (kind[j] == 1.0) {
         const double e = 1.0 - dl;
         lr += -0.5 * log(u * u + e * e);
         ph -= atan2(u, e);
@@ -112,7 +121,7 @@ __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, doubl
   // one warp per core k; lanes draw slots (first attempts) or coordinates (redraws) in
   // parallel, duplicates are resolved slot by slot in order, so the accepted sets
   // are those of a plain sequential draw
-  for (int k = 1 + warp; k < d; k += kWarps) {
+  for (int k = 1 + warp; draw && k < d; k += kWarps) {
     const int width = d - k;
     const long long cap = jd.rmax;
     long long rk = ipow_cap(n, k, cap + 1);
@@ -1484,6 +1493,18 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
       lset_at(x, k + 1, t)[pos] = pos < k ? lset_at(x, k, g / N)[pos] : (uint16_t)(g % N);
     }
     if (tid == 0) x.lsz[k + 1] = rho;
+    if (x.emit) {  // two-train form: this core's skeleton (the latest left-to-right one stays)
+      int* er = reinterpret_cast<int*>(x.emit + (size_t)k * emit_core_bytes(x.rall, x.dmax));
+      int* ew = er + 1;
+      uint16_t* ek = reinterpret_cast<uint16_t*>(ew + x.rall);
+      const int wr = x.d - k - 1;
+      if (tid == 0) er[0] = rho;
+      for (int t = tid; t < rho; t += kThreads) ew[t] = x.wrow[t];
+      for (int idx = tid; idx < rho * wr; idx += kThreads) {
+        const int t = idx / wr, pos = idx % wr;
+        ek[t * x.dmax + pos] = rset_at(x, k + 1, x.jp[t])[pos];
+      }
+    }
   } else {
     const int w = x.d - k;
     for (int idx = tid; idx < rho * w; idx += kThreads) {

@@ -106,6 +106,7 @@ template <> struct Num<float> {
   __device__ static __forceinline__ float ex(float e) { return exp2f(e); }
   __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   __device__ static __forceinline__ double unscale(double shift) { return exp2(shift); }
+  __device__ static __forceinline__ double log_unscale(double shift) { return shift * 0.6931471805599453; }
   __device__ static __forceinline__ float ceil_(float v) { return ceilf(v); }
   __device__ static __forceinline__ float logu(float v) { return __log2f(v); }
 };
@@ -115,6 +116,7 @@ template <> struct Num<double> {
   __device__ static __forceinline__ double ex(double e) { return exp(e); }
   __device__ static __forceinline__ double div(double a, double b) { return a / b; }
   __device__ static __forceinline__ double unscale(double shift) { return exp(shift); }
+  __device__ static __forceinline__ double log_unscale(double shift) { return shift; }
   __device__ static __forceinline__ double ceil_(double v) {
     return ceil(v * 1.4426950408889634) * 0.6931471805599453;
   }
@@ -124,17 +126,30 @@ template <> struct Num<double> {
 // ---------------------------------------------------------------------------
 // descriptors shared with the host
 // ---------------------------------------------------------------------------
+// What a job's train approximates: the pricing integrand, or (two-train form,
+// Eq. braket) one of its two factors.
+enum : int { FACTOR_PRODUCT = 0, FACTOR_VHAT = 1, FACTOR_PHI = 2 };
+
 struct JobDesc {
   int d, n, rmax, instance;
   int cauchy;     // 1: min-call, has the 1/(D0 + i sum u) factor
   int term;       // max-call term (0 for the min-call): selects the pivot stream
   int param_off;  // doubles: cov[d*d] row-major, delta[d], pcoef[d], kind[d]
-  int pad;
+  int factor;     // FACTOR_*
   unsigned long long seed;
   double T, D0, L;
+  double Tq;      // time factor of the Gaussian exponent -Tq/2 u^T Cov u (0: no Gaussian)
   double logscale, sign, weight;  // true integrand = sign*exp(logscale + sum norms)*value
   double cap;  // no-arbitrage bound on the train's share of the price: the sum of the spots
 };
+
+// Skeleton of a factor train's core k (two-train form), written by the cross at
+// each left-to-right core: rank rho, the selected fiber rows W[t] = o N + i (o
+// the outer index), the kept columns' multi-indices K[t][pos] over axes
+// k+1..d-1, t in pivot-row order.  One record of emit_core_bytes per core.
+__host__ __device__ inline size_t emit_core_bytes(int rall, int dmax) {
+  return ((size_t)4 + 4 * (size_t)rall + 2 * (size_t)rall * dmax + 15) / 16 * 16;
+}
 
 struct JobResult {
   double est_re, est_im;  // TT sum of the normalised integrand
@@ -321,6 +336,7 @@ struct Ctx {
   uint32_t tmem, tmem_cols, mma_phase;  // mma_phase: bit k = next parity of barrier k
   int tc_pending;  // a completion wait gave up: wait again before releasing TMEM
   int fail_step;
+  char* emit;      // two-train form: this job's skeleton records (NULL: none)
 };
 
 // Index sets: left set at bond k holds multi-indices over axes 0..k-1,

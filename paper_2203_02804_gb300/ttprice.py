@@ -32,6 +32,9 @@ TT_ENGINE_AUTO = 0
 TT_ENGINE_CUDA_CORES = 1
 TT_ENGINE_TENSOR_CORES = 2
 ENGINES = {"auto": TT_ENGINE_AUTO, "cuda": TT_ENGINE_CUDA_CORES, "tc": TT_ENGINE_TENSOR_CORES}
+TT_METHOD_SINGLE_TRAIN = 0
+TT_METHOD_TWO_TRAINS = 1
+METHODS = {"single": TT_METHOD_SINGLE_TRAIN, "two-train": TT_METHOD_TWO_TRAINS}
 
 EXPORTS = ("tt_price_create", "tt_workspace_bytes", "tt_price_evaluate", "tt_price_prepare",
            "tt_price_run", "tt_price_results", "tt_price_transfer_bytes", "tt_price_destroy",
@@ -53,7 +56,7 @@ class tt_options(ctypes.Structure):
                 ("max_half_sweeps", ctypes.c_int), ("sweep_tol", ctypes.c_double),
                 ("rank_tol", ctypes.c_double), ("maxvol_tol", ctypes.c_double),
                 ("block_rows", ctypes.c_int), ("engine", ctypes.c_int), ("graph", ctypes.c_int),
-                ("device", ctypes.c_int),
+                ("method", ctypes.c_int), ("device", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -191,7 +194,7 @@ class Pricer:
                  precision: str = "fp64", device: int = 0, stream=None, max_half_sweeps: int = 0,
                  sweep_tol: float = 0.0, rank_tol: float = 0.0, maxvol_tol: float = 0.0,
                  block_rows: int = 0, use_torch_workspace: bool = True, engine: str = "auto",
-                 graph: bool = True):
+                 graph: bool = True, method: str = "single"):
         import torch  # device memory and streams only
 
         if not torch.cuda.is_available():
@@ -208,6 +211,7 @@ class Pricer:
         o.block_rows = block_rows
         o.engine = ENGINES[engine]
         o.graph = 1 if graph else 0
+        o.method = METHODS[method]
         o.device = device
         with torch.cuda.device(device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(device)

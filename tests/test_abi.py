@@ -62,6 +62,11 @@ def test_create_rejects_bad_options_without_touching_the_gpu(lib):
     assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
     o.engine = 3
     assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    # the two-train form: a method out of range, or ranks above its 32
+    o.engine, o.method = ttprice.TT_ENGINE_AUTO, 2
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    o.method, o.max_rank, o.block_rows = ttprice.TT_METHOD_TWO_TRAINS, 64, 128
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
     lib.tt_price_destroy(None)
 
 
@@ -71,9 +76,9 @@ def test_struct_layouts_match_c():
     #include <stddef.h>
     #include "ttprice.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(tt_options), offsetof(tt_options, sweep_tol),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tt_options), offsetof(tt_options, sweep_tol),
              offsetof(tt_options, block_rows), offsetof(tt_options, engine), offsetof(tt_options, graph),
-             offsetof(tt_options, cuda_stream),
+             offsetof(tt_options, method), offsetof(tt_options, cuda_stream),
              offsetof(tt_options, workspace_bytes));
       printf("%zu %zu %zu %zu %zu\n", sizeof(tt_problem), offsetof(tt_problem, rate),
              offsetof(tt_problem, damping), offsetof(tt_problem, trunc_L), offsetof(tt_problem, seed));
@@ -91,8 +96,8 @@ def test_struct_layouts_match_c():
     T = ttprice
     want = [
         [ctypes.sizeof(T.tt_options), T.tt_options.sweep_tol.offset, T.tt_options.block_rows.offset,
-         T.tt_options.engine.offset, T.tt_options.graph.offset, T.tt_options.cuda_stream.offset,
-         T.tt_options.workspace_bytes.offset],
+         T.tt_options.engine.offset, T.tt_options.graph.offset, T.tt_options.method.offset,
+         T.tt_options.cuda_stream.offset, T.tt_options.workspace_bytes.offset],
         [ctypes.sizeof(T.tt_problem), T.tt_problem.rate.offset, T.tt_problem.damping.offset,
          T.tt_problem.trunc_L.offset, T.tt_problem.seed.offset],
         [ctypes.sizeof(T.tt_diag), T.tt_diag.evaluations.offset, T.tt_diag.fail_step.offset,
