@@ -107,7 +107,14 @@ def _oracle_one(args):
     return price
 
 
-def oracle_prices(problems, workers):
+def _oracle_two(args):
+    from oracle import twomps
+
+    price, _, _ = twomps.two_train_price(args)
+    return price
+
+
+def oracle_prices(problems, workers, fn=None):
     import multiprocessing as mp
 
     os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -116,7 +123,7 @@ def oracle_prices(problems, workers):
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(workers) as pool:
-        out = pool.map(_oracle_one, problems, chunksize=1)
+        out = pool.map(fn or _oracle_one, problems, chunksize=1)
     return out, time.perf_counter() - t0
 
 
@@ -259,6 +266,52 @@ def measure_surrogate(args, tuned):
     return out
 
 
+def measure_two_train(args, workers):
+    """The paper's two-train (bra-ket) form against the single train on the paper's
+    own d=5 setting (Section V: r=0.3, sigma=0.5, beta=0.5, S0=K=100, N=50, bond
+    dimension 15, seeds varied), mixed path, L2 flushed between steps: device
+    throughput of both forms (CUDA events around tt_price_run), and the two-train
+    prices of the first problems against the oracle's two-train price."""
+    import torch
+
+    from paper_2203_02804_gb300 import inputs, ttprice
+
+    probs = [inputs.paper_table_problem(5).with_(seed=5000 + i) for i in range(args.two_train_batch)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"workload": "paper-d5 min-call, N=50, rank 15, mixed", "batch": len(probs)}
+    prices = None
+    for meth in ("two-train", "single"):
+        pr = ttprice.Pricer(max_d=5, max_n=50, max_rank=15, max_batch=len(probs), precision="mixed",
+                            method=meth, graph=True)
+        pr.prepare(probs)
+        for _ in range(3):
+            pr.run()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(pr.stream)
+            pr.run()
+            b.record(pr.stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        rc, pv, diags = pr.results()
+        pr.close()
+        key = "two_train" if meth == "two-train" else "single_train"
+        out[key] = {"prices_per_s": len(probs) / (statistics.median(ts) / 1e3), "ms": statistics.median(ts),
+                    "status_counts": {str(v): sum(1 for d in diags if d.status == v)
+                                      for v in sorted({d.status for d in diags})}}
+        if meth == "two-train":
+            prices = pv
+    n = min(args.cpu_sample, len(probs))
+    if n:
+        ref, dt = oracle_prices(probs[:n], min(workers, n), fn=_oracle_two)
+        out["parity"] = {"vs": "FP64 oracle two-train price, same problems", "n": n,
+                         "max_rel_err": max(abs(prices[i] / ref[i] - 1.0) for i in range(n)), "tol": 1e-4}
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -340,6 +393,9 @@ def run_gpu(args):
     surrogate = None
     if args.surrogate_samples > 0 and world == 1:
         surrogate = measure_surrogate(args, tuned)
+    two_train = None
+    if args.two_train_batch > 0 and world == 1:
+        two_train = measure_two_train(args, cpu_workers())
 
     if rank == 0:
         clocks = clk.summary()
@@ -369,6 +425,8 @@ def run_gpu(args):
         }
         if surrogate is not None:
             line["surrogate"] = surrogate
+        if two_train is not None:
+            line["two_train"] = two_train
         if sample is not None:
             sp, sprices, sdt, workers = sample
             n = len(sp)
@@ -398,6 +456,8 @@ def main():
     ap.add_argument("--surrogate-samples", type=int, default=1 << 18,
                     help="TT-priced training samples of the learned surrogate (0: skip it)")
     ap.add_argument("--surrogate-epochs", type=int, default=24)
+    ap.add_argument("--two-train-batch", type=int, default=4096,
+                    help="problems of the paper's d=5 setting priced in the two-train form (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -368,9 +368,10 @@ __global__ void finalize_kernel(const JobDesc* __restrict__ jobs, const JobResul
 //   A_k(i) = F(I_{k-1}, i, K_k),  P_k = A_k[W_k],  G_k(i) = A_k(i) P_k^{-1}
 // (the shifts cancel in G), the end core G(i) = F(I_{d-2}, i); then
 //   E <- sum_i G^v_k(i)^T E G^phi_k(i),  E_0 = [1].
-// P_k^{-1} comes from FP64 Gauss-Jordan with partial pivoting; G and the
-// contraction run in R.  The bracket, in the v train's normalised units, goes
-// to that train's result; the phi train's carries no price.
+// Regrouped, E <- (P^v_k)^{-T} [sum_i A^v_k(i)^T E A^phi_k(i)] (P^phi_k)^{-1}, so
+// the inverses (FP64 Gauss-Jordan with partial pivoting) apply once per core.
+// The bracket, in the v train's normalised units, goes to that train's result;
+// the phi train's carries no price.
 // ---------------------------------------------------------------------------
 struct BrSmem {
   int tab[2], cshift[2], cref[2], lsz[2], rsz[2], W[2];
@@ -562,58 +563,124 @@ __global__ void __launch_bounds__(kThreads, 1) bracket_kernel(const JobDesc* __r
       cpx<R> acc[kAcc];
 #pragma unroll
       for (int q = 0; q < kAcc; ++q) acc[q] = cpx<R>{R(0), R(0)};
-      for (int i = 0; i < N; ++i) {
-        for (int idx = tid; idx < rpv * rkv; idx += kThreads) Av[idx] = eval_point(xs[0], idx / rkv, i, idx % rkv);
-        for (int idx = tid; idx < rpf * rkf; idx += kThreads) Af[idx] = eval_point(xs[1], idx / rkf, i, idx % rkf);
-        __syncthreads();
-        const cpx<R>* gv = Av;
-        const cpx<R>* gf = Af;
-        if (!last) {  // G(i) = A(i) P^{-1}
-          for (int idx = tid; idx < rpv * rkv; idx += kThreads) {
-            const int a = idx / rkv, t = idx % rkv;
-            cpx<R> s2 = {R(0), R(0)};
-            for (int c = 0; c < rkv; ++c) cfma(s2, Av[a * rkv + c], Mv[c * rkv + t]);
-            Gv[idx] = s2;
+      // Walks along the grid index: for a fixed fiber pair (a, b) the exponent is
+      // e0 - shift + h u_i + tl(i) with u_i = u_0 + i eta, so exp(e0 - shift + h u_i)
+      // is stepped by the factor exp(h eta) and exp(tl(i)) comes from a table; a
+      // pair whose exponent range would leave FP64 is evaluated directly.  Thread
+      // tid owns entries tid + q kThreads of each factor's A(i).
+      R wcur[2][kAcc], wstep[2][kAcc], ws0[2][kAcc];
+      cpx<R> wph[2][kAcc];
+      unsigned wdir = 0;
+      {
+        const R eta = (R)(2.0 * jv.L / N);
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const Ctx<R>& x = xs[f];
+          R* tex = reinterpret_cast<R*>(smem + S.tab[f]) + 4 * lay.nmax;
+          for (int i = tid; i < N; i += kThreads) tex[i] = Num<R>::ex(x.tl[i]);
+          const int rp = x.lsz[k], rk = last ? 1 : x.rsz[k + 1];
+#pragma unroll
+          for (int q = 0; q < kAcc; ++q) {
+            const int idx = tid + q * kThreads;
+            wcur[f][q] = wstep[f][q] = ws0[f][q] = R(0);
+            wph[f][q] = cpx<R>{R(0), R(0)};
+            if (idx < rp * rk) {
+              const int a = idx / rk, b = idx % rk;
+              const PairE<R> pq = x.pair[a * x.rall + b];
+              const R e = pq.e0 - x.cshift[b] + pq.h * x.tu[0], he = pq.h * eta;
+              if (fabs((double)e) < 600.0 && fabs((double)he) * N < 100.0) {
+                wcur[f][q] = Num<R>::ex(e);
+                wstep[f][q] = Num<R>::ex(he);
+              } else {
+                wdir |= 1u << (f * kAcc + q);
+              }
+              ws0[f][q] = pq.s0;
+              wph[f][q] = cpx<R>{pq.ore, pq.oim};
+            }
           }
-          for (int idx = tid; idx < rpf * rkf; idx += kThreads) {
-            const int b = idx / rkf, t = idx % rkf;
-            cpx<R> s2 = {R(0), R(0)};
-            for (int c = 0; c < rkf; ++c) cfma(s2, Af[b * rkf + c], Mf[c * rkf + t]);
-            Gf[idx] = s2;
-          }
-          __syncthreads();
-          gv = Gv;
-          gf = Gf;
         }
-        // X = E G^phi(i): rpv x rkf
+        __syncthreads();
+      }
+      // Et = sum_i A^v(i)^T E A^phi(i), then E <- (P^v)^{-T} Et (P^phi)^{-1}: the
+      // inverses leave the grid loop (G(i)^T E G(i) with G = A P^{-1}, regrouped)
+      for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const Ctx<R>& x = xs[f];
+          const R* tex = reinterpret_cast<const R*>(smem + S.tab[f]) + 4 * lay.nmax;
+          const int rp = x.lsz[k], rk = last ? 1 : x.rsz[k + 1];
+          cpx<R>* A = f ? Af : Av;
+          const cpx<R> tph = {x.tor[i], x.toi[i]};
+          const R ui = x.tu[i], tx = tex[i];
+#pragma unroll
+          for (int q = 0; q < kAcc; ++q) {
+            const int idx = tid + q * kThreads;
+            if (idx < rp * rk) {
+              if ((wdir >> (f * kAcc + q)) & 1u) {
+                A[idx] = eval_point(x, idx / rk, i, idx % rk);
+              } else {
+                R mag = wcur[f][q] * tx;
+                cpx<R> w = cmul(wph[f][q], tph);
+                if (x.cauchy) {
+                  const R sv = ws0[f][q] + ui;
+                  mag = Num<R>::div(mag, fma(sv, sv, x.D0 * x.D0));
+                  w = cmul(w, cpx<R>{x.D0, -sv});
+                }
+                A[idx] = cpx<R>{w.re * mag, w.im * mag};
+                wcur[f][q] *= wstep[f][q];
+              }
+            }
+          }
+        }
+        __syncthreads();
+        // X = E A^phi(i): rpv x rkf
         for (int idx = tid; idx < rpv * rkf; idx += kThreads) {
           const int a = idx / rkf, t = idx % rkf;
           cpx<R> s2 = {R(0), R(0)};
-          for (int b = 0; b < rpf; ++b) cfma(s2, E[a * rpf + b], gf[b * rkf + t]);
+          for (int b = 0; b < rpf; ++b) cfma(s2, E[a * rpf + b], Af[b * rkf + t]);
           X[idx] = s2;
         }
         __syncthreads();
-        // acc(a', b') += sum_a G^v(i)[a][a'] X[a][b']
+        // acc(a', b') += sum_a A^v(i)[a][a'] X[a][b']
 #pragma unroll
         for (int q = 0; q < kAcc; ++q) {
           const int idx = tid + q * kThreads;
           if (idx < rkv * rkf) {
             const int ap = idx / rkf, bp = idx % rkf;
-            for (int a = 0; a < rpv; ++a) cfma(acc[q], gv[a * rkv + ap], X[a * rkf + bp]);
+            for (int a = 0; a < rpv; ++a) cfma(acc[q], Av[a * rkv + ap], X[a * rkf + bp]);
           }
         }
         __syncthreads();
       }
+      if (last) {
+        if (tid == 0) E[0] = acc[0];
+      } else {
+        // Y = Et (P^phi)^{-1} into Gf, then E = (P^v)^{-T} Y
 #pragma unroll
-      for (int q = 0; q < kAcc; ++q) {
-        const int idx = tid + q * kThreads;
-        if (idx < rkv * rkf) E[idx] = acc[q];
+        for (int q = 0; q < kAcc; ++q) {
+          const int idx = tid + q * kThreads;
+          if (idx < rkv * rkf) Gv[idx] = acc[q];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < rkv * rkf; idx += kThreads) {
+          const int ap = idx / rkf, t = idx % rkf;
+          cpx<R> s2 = {R(0), R(0)};
+          for (int c = 0; c < rkf; ++c) cfma(s2, Gv[ap * rkf + c], Mf[c * rkf + t]);
+          Gf[idx] = s2;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < rkv * rkf; idx += kThreads) {
+          const int s3 = idx / rkf, t = idx % rkf;
+          cpx<R> s2 = {R(0), R(0)};
+          for (int c = 0; c < rkv; ++c) cfma(s2, Mv[c * rkv + s3], Gf[c * rkf + t]);
+          E[idx] = s2;
+        }
       }
       if (tid == 0) {
         const double pts = (double)N * (rpv * rkv + rpf * rkf);
         xs[0].evals += (long long)pts;
-        xs[0].flops += 24.0 * pts + 8.0 * N * ((last ? 0.0 : (double)rpv * rkv * rkv + (double)rpf * rkf * rkf) +
-                                               (double)rpv * rpf * rkf + (double)rpv * rkv * rkf);
+        xs[0].flops += 24.0 * pts + 8.0 * (N * ((double)rpv * rpf * rkf + (double)rpv * rkv * rkf) +
+                                           (last ? 0.0 : (double)rkv * rkf * (rkf + rkv)));
       }
       // next core's left sets: I_k[t] = I_{k-1}[W[t] / N] followed by W[t] % N
       if (!last) {
@@ -805,7 +872,7 @@ ttp::BrSmem make_brsmem(const tt_options& o, bool f64) {
     return at;
   };
   for (int f = 0; f < 2; ++f) {
-    S.tab[f] = take(4 * n * rs);
+    S.tab[f] = take(5 * n * rs);  // tl, tu, tor, toi, exp(tl)
     S.cshift[f] = take((r + 1) * rs);
     S.cref[f] = take((r + 1) * rs);
     S.lsz[f] = take((d + 1) * 4);
