@@ -479,16 +479,17 @@ __device__ void bracket_ctx(Ctx<R>& x, const JobDesc& jd, const double* params, 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 1) bracket_kernel(const JobDesc* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, 2) bracket_kernel(const JobDesc* __restrict__ jobs,
                                                               const double* __restrict__ params,
                                                               const int2* __restrict__ pairs, int npairs,
                                                               const char* __restrict__ emit, size_t emit_stride,
-                                                              JobResult* results, char* scratch, Layout lay,
-                                                              BrSmem S) {
+                                                              int* counter, JobResult* results, char* scratch,
+                                                              Layout lay, BrSmem S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double dscr[32];
   __shared__ Ctx<R> xs[2];
   __shared__ int misc[16];
+  __shared__ int slot;
   const int tid = threadIdx.x;
   const size_t ecb = emit_core_bytes(lay.rmax, lay.dmax);
   cpx<R>* E = reinterpret_cast<cpx<R>*>(smem + S.E);
@@ -500,7 +501,12 @@ __global__ void __launch_bounds__(kThreads, 1) bracket_kernel(const JobDesc* __r
   double* redv = reinterpret_cast<double*>(smem + S.red);
   int* redi = reinterpret_cast<int*>(redv + 2);
   constexpr int kAcc = 4;  // accumulator entries per thread: rank <= 32 on both trains
-  for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+  for (;;) {  // brackets from a queue: a CTA that shares its SM takes fewer
+    __syncthreads();  // every thread has read the previous slot
+    if (tid == 0) slot = atomicAdd(counter, 1);
+    __syncthreads();
+    const int pr = slot;
+    if (pr >= npairs) break;
     const int2 jp = pairs[pr];
     const JobDesc jv = jobs[jp.x], jf = jobs[jp.y];
     if (results[jp.x].status < 0 || results[jp.y].status < 0) continue;  // a train failed: the price is NaN
@@ -1309,7 +1315,7 @@ int launch_all(tt_pricer* h, cudaStream_t stream) {
   JobResult* jres = reinterpret_cast<JobResult*>(h->ws + h->dl.jres);
   InstanceResult* ires = reinterpret_cast<InstanceResult*>(h->ws + h->dl.ires);
   char* scratch = h->ws + h->dl.scratch;
-  if (cudaMemsetAsync(counter, 0, sizeof(int), stream) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaMemsetAsync(counter, 0, 2 * sizeof(int), stream) != cudaSuccess) return TT_ERR_CUDA;
   char* emit = h->ws + h->dl.emit;
   const size_t es = h->dl.emit_stride;
   if (h->njobs > 0) {
@@ -1332,7 +1338,7 @@ int launch_all(tt_pricer* h, cudaStream_t stream) {
     // and the cores G = A P^{-1} are formed from FP64 integrand values (P can be
     // conditioned up to 1/rank_tol, which FP32 values would turn into 1e-3 errors)
     ttp::bracket_kernel<double><<<bg, ttp::kThreads, h->bsm.total, stream>>>(
-        jobs, params, pairs, h->npairs, emit, es, jres, scratch, h->lay, h->bsm);
+        jobs, params, pairs, h->npairs, emit, es, counter + 1, jres, scratch, h->lay, h->bsm);
     if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
   }
   if (h->count > 0) {
@@ -1458,7 +1464,16 @@ int tt_price_create(const tt_options* opt, tt_pricer** out) {
       delete h;
       return TT_ERR_CAPACITY;
     }
-    h->bgrid = std::max(1, grid / 2);
+    // every CTA resident (they share the queue); two scratch blocks each
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttp::bracket_kernel<double>, ttp::kThreads,
+                                                      h->bsm.total) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, R.o.device) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+      sms = grid / 2;
+    }
+    h->bgrid = std::max(1, std::min(grid / 2, std::max(1, per_sm) * sms));
   }
   h->dl = make_dev_layout(R, h->lay, grid);
   h->stream = reinterpret_cast<cudaStream_t>(R.o.cuda_stream);
