@@ -91,7 +91,8 @@ typedef struct {
                            TT_ENGINE_AUTO picks CUDA cores up to max_rank 32 and
                            tensor cores above; TT_FP64 always uses CUDA cores    */
   int graph;            /* 1: tt_price_run replays a CUDA graph of its launches
-                           (counter reset, TT-cross kernel, finalize), captured
+                           (counter reset, TT-cross kernel, the bracket kernel
+                           in the two-train form, finalize), captured
                            once per batch layout on a stream the pricer owns and
                            ordered after / before cuda_stream by events; 0: plain
                            launches on cuda_stream                               */

@@ -188,7 +188,12 @@ class ProblemBatch:
 
 
 class Pricer:
-    """Owns one tt_pricer handle on a CUDA device, with a torch-allocated workspace."""
+    """Owns one tt_pricer handle on a CUDA device, with a torch-allocated workspace.
+
+    ``method`` = "single" crosses the product integrand (one train per term);
+    "two-train" is the paper's bra-ket form (Section IV, Eq. braket): separate
+    trains of the payoff transform and the characteristic function, contracted
+    site by site (rank <= 32, N <= 1024)."""
 
     def __init__(self, max_d: int, max_n: int, max_rank: int, max_batch: int,
                  precision: str = "fp64", device: int = 0, stream=None, max_half_sweeps: int = 0,
