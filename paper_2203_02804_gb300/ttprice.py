@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+from collections import abc
 from dataclasses import dataclass
 from typing import Optional, Sequence
 
@@ -138,6 +139,43 @@ class Diag:
     maxvol_rollbacks: int
     imag_part: float
     flops: float
+
+
+# tt_diag as a NumPy record (same offsets as the C struct)
+DIAG_DTYPE = np.dtype({
+    "names": [f for f, _ in tt_diag._fields_],
+    "formats": [np.int32 if t is ctypes.c_int else np.int64 if t is ctypes.c_longlong else np.float64
+                for _, t in tt_diag._fields_],
+    "offsets": [getattr(tt_diag, f).offset for f, _ in tt_diag._fields_],
+    "itemsize": ctypes.sizeof(tt_diag),
+})
+
+
+class DiagList(abc.Sequence):
+    """The per-problem diagnostics of a batch as a sequence of Diag, converted from
+    the C array column by column on first access (a caller that ignores them pays
+    nothing)."""
+
+    def __init__(self, carray, n: int):
+        self._c = carray
+        self._n = n
+        self._items = None
+
+    def _materialise(self):
+        if self._items is None:
+            rec = np.frombuffer(self._c, dtype=DIAG_DTYPE, count=self._n)
+            cols = [rec[f].tolist() for f in DIAG_DTYPE.names]
+            self._items = [Diag(*row) for row in zip(*cols)]
+        return self._items
+
+    def __len__(self):
+        return self._n
+
+    def __getitem__(self, i):
+        return self._materialise()[i]
+
+    def __iter__(self):
+        return iter(self._materialise())
 
 
 # tt_problem as a NumPy record (same offsets as the C struct; checked by the tests)
@@ -271,8 +309,7 @@ class Pricer:
         prices = (ctypes.c_double * max(1, n))()
         diags = (tt_diag * max(1, n))()
         rc = self.lib.tt_price_results(self.handle, prices, diags)
-        return rc, np.array(prices[:n]), [Diag(*(getattr(d, f) for f, _ in tt_diag._fields_))
-                                          for d in diags[:n]]
+        return rc, np.frombuffer(prices, dtype=np.float64, count=n).copy(), DiagList(diags, n)
 
     def transfer_bytes(self):
         """(host-to-device bytes of the last prepare, device-to-host bytes of the last results)."""
@@ -281,11 +318,10 @@ class Pricer:
         return int(h2d.value), int(d2h.value)
 
     def evaluate(self, problems):
-        """Price a batch; returns (worst status, prices ndarray, list of Diag)."""
+        """Price a batch; returns (worst status, prices ndarray, sequence of Diag)."""
         batch = ProblemBatch(problems)
         n = batch.count
         prices = (ctypes.c_double * max(1, n))()
         diags = (tt_diag * max(1, n))()
         rc = self.lib.tt_price_evaluate(self.handle, batch.arr, n, prices, diags)
-        return rc, np.array(prices[:n]), [Diag(*(getattr(d, f) for f, _ in tt_diag._fields_))
-                                          for d in diags[:n]]
+        return rc, np.frombuffer(prices, dtype=np.float64, count=n).copy(), DiagList(diags, n)
