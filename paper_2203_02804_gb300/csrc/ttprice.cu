@@ -544,7 +544,25 @@ __global__ void __launch_bounds__(kThreads, 2) bracket_kernel(const JobDesc* __r
         __syncthreads();
         core_states(x, k, DIR_LR);
         load_axis_table(x, k);
-        column_shifts(x, rp, rk);
+        if (last) {
+          column_shifts(x, rp, rk);
+        } else {
+          // shifts from the pivot rows alone: the skeleton's rows dominate (maxvol:
+          // |A P^{-1}| <= 1 + tau), so a column's largest fiber entry is at most
+          // (1 + tau) rk times its largest pivot-row entry, well inside the range
+          const int lane = tid & 31, warp = tid >> 5;
+          for (int c = warp; c < rk; c += kWarps) {
+            R mx = R(-1e300);
+            for (int t = lane; t < rk; t += 32) {
+              const int g = W[t];
+              mx = fmax(mx, eval_logmag(x, g / N, g % N, c));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+            if (lane == 0) x.cshift[c] = Num<R>::ceil_(mx);
+          }
+          __syncthreads();
+        }
         if (!last) {
           // the pivot block A[W, :] in FP64, inverted
           double2* G = reinterpret_cast<double2*>(smem + S.X);
