@@ -455,7 +455,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--surrogate-samples", type=int, default=1 << 18,
                     help="TT-priced training samples of the learned surrogate (0: skip it)")
-    ap.add_argument("--surrogate-epochs", type=int, default=24)
+    ap.add_argument("--surrogate-epochs", type=int, default=40)
     ap.add_argument("--two-train-batch", type=int, default=4096,
                     help="problems of the paper's d=5 setting priced in the two-train form (0: skip)")
     args = ap.parse_args()

@@ -204,9 +204,11 @@ class ProblemBatch:
             self.arr = self.rec.ctypes.data_as(ctypes.POINTER(tt_problem))
             return
         d = np.fromiter((len(p.spot) for p in problems), dtype=np.int64, count=n)
-        self.spot = np.concatenate([np.asarray(p.spot, dtype=np.float64).ravel() for p in problems])
-        self.cov = np.concatenate([np.asarray(p.cov, dtype=np.float64).ravel() for p in problems])
-        self.damp = np.concatenate([np.asarray(p.damping, dtype=np.float64).ravel() for p in problems])
+        self.spot = np.concatenate([p.spot for p in problems], axis=None, dtype=np.float64)
+        self.cov = np.concatenate([p.cov for p in problems], axis=None, dtype=np.float64)
+        self.damp = np.concatenate([p.damping for p in problems], axis=None, dtype=np.float64)
+        if self.cov.size != int(np.sum(d * d)) or self.damp.size != self.spot.size:
+            raise ValueError("each problem needs spot[d], cov[d][d] and damping[d]")
         off1 = np.concatenate([[0], np.cumsum(d)[:-1]])
         off2 = np.concatenate([[0], np.cumsum(d * d)[:-1]])
         r = self.rec
@@ -214,13 +216,12 @@ class ProblemBatch:
         r["spot"] = self.spot.ctypes.data + 8 * off1
         r["cov"] = self.cov.ctypes.data + 8 * off2
         r["damping"] = self.damp.ctypes.data + 8 * off1
-        r["rate"] = [float(p.rate) for p in problems]
-        r["maturity"] = [float(p.maturity) for p in problems]
-        r["strike"] = [float(p.strike) for p in problems]
-        r["payoff"] = [TT_MIN_CALL if p.payoff == "min" else TT_MAX_CALL for p in problems]
-        r["n_grid"] = [int(p.n_grid) for p in problems]
-        r["trunc_L"] = [float(p.trunc_L) for p in problems]
-        r["max_rank"] = [int(p.max_rank) for p in problems]
+        sc = np.array([(p.rate, p.maturity, p.strike, p.trunc_L) for p in problems], dtype=np.float64)
+        r["rate"], r["maturity"], r["strike"], r["trunc_L"] = sc[:, 0], sc[:, 1], sc[:, 2], sc[:, 3]
+        ints = np.array([(0 if p.payoff == "min" else 1, p.n_grid, p.max_rank) for p in problems], dtype=np.int64)
+        r["payoff"] = np.where(ints[:, 0] == 0, TT_MIN_CALL, TT_MAX_CALL)
+        r["n_grid"] = ints[:, 1]
+        r["max_rank"] = ints[:, 2]
         r["seed"] = [int(p.seed) & ((1 << 64) - 1) for p in problems]
         self.arr = r.ctypes.data_as(ctypes.POINTER(tt_problem))
 
