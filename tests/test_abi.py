@@ -8,6 +8,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_2203_02804_gb300 import build, ttprice
@@ -129,3 +130,39 @@ def test_problem_batch_packs_pointers():
         assert [rec.damping[j] for j in range(p.d)] == list(np.asarray(p.damping, dtype=float))
         assert rec.payoff == (ttprice.TT_MIN_CALL if p.payoff == "min" else ttprice.TT_MAX_CALL)
         assert rec.seed == p.seed
+
+
+def test_problem_batch_packs_every_field():
+    """The packed tt_problem records point at each problem's own spot, covariance
+    and damping values and carry its scalars (heterogeneous d, both payoffs)."""
+    from paper_2203_02804_gb300 import inputs
+
+    probs = inputs.mixed_batch(24)
+    b = ttprice.ProblemBatch(probs)
+    assert b.count == len(probs)
+    dbl = ctypes.POINTER(ctypes.c_double)
+    for p, r in zip(probs, b.rec):
+        d = p.d
+        assert int(r["d"]) == d
+        for name, want in (("spot", p.spot), ("cov", np.ravel(p.cov)), ("damping", p.damping)):
+            got = np.ctypeslib.as_array(ctypes.cast(int(r[name]), dbl), shape=(np.size(want),))
+            assert np.array_equal(got, np.asarray(want, dtype=np.float64)), name
+        assert float(r["rate"]) == p.rate and float(r["maturity"]) == p.maturity
+        assert float(r["strike"]) == p.strike and float(r["trunc_L"]) == p.trunc_L
+        assert int(r["payoff"]) == (ttprice.TT_MIN_CALL if p.payoff == "min" else ttprice.TT_MAX_CALL)
+        assert int(r["n_grid"]) == p.n_grid and int(r["max_rank"]) == p.max_rank
+        assert int(r["seed"]) == p.seed
+
+
+def test_diag_list_reads_the_c_array():
+    """Per-problem diagnostics come back as a sequence of Diag read from the C
+    array (all field types: int, long long, double)."""
+    c = (ttprice.tt_diag * 3)()
+    c[1].status, c[1].evaluations, c[1].fail_step = ttprice.TT_ERR_NUMERIC, 123456789012, 9
+    c[2].imag_part, c[2].maxvol_rollbacks, c[2].flops, c[2].terms = -0.25, 7, 1.5e12, 10
+    dl = ttprice.DiagList(c, 3)
+    assert len(dl) == 3
+    assert dl[1].status == ttprice.TT_ERR_NUMERIC and dl[1].evaluations == 123456789012 and dl[1].fail_step == 9
+    assert dl[2].imag_part == -0.25 and dl[2].maxvol_rollbacks == 7 and dl[2].flops == 1.5e12
+    assert [d.terms for d in dl] == [0, 0, 10]
+    assert dl[-1] == dl[2] and len(dl[:2]) == 2
