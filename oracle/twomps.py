@@ -41,7 +41,8 @@ Pins (tests/test_oracle_twomps.py): the contraction against the dense sum of
 two small random trains built out by brute force; the two factors' product
 against the single-train integrand; the full-rank bracket against the full
 grid sum; the rank-1 train of the characteristic function without correlation
-against the product of one-dimensional sums; the d=2 price against Stulz.
+against the product of one-dimensional sums; the d=2 min-call and max-call prices
+against Stulz's closed forms; the paper's d=3, 4 setting against the full grid sum.
 """
 from __future__ import annotations
 

@@ -92,3 +92,14 @@ def test_paper_setting_batch_agrees_with_single_train(tp):
     for i in (0, 1, 2, 3, 4):
         ref, _, _ = twomps.two_train_price(probs[i])
         assert abs(two[i] / ref - 1) < 1e-4
+
+
+def test_tensor_core_factor_crosses(tp):
+    """The factor crosses on the tensor-core engine (3xTF32 block products), mixed:
+    the bracket matches the oracle's two-train price to 1e-4."""
+    for d, payoff in ((3, "min"), (3, "max")):
+        p = inputs.paper_table_problem(d).with_(payoff=payoff)
+        rc, prices, diags = _price(tp, [p], "mixed", engine="tc")
+        ref, _, _ = twomps.two_train_price(p)
+        assert diags[0].status == tp.TT_OK
+        assert abs(prices[0] / ref - 1) < 1e-4, (payoff, prices[0], ref)
