@@ -103,3 +103,22 @@ def test_tensor_core_factor_crosses(tp):
         ref, _, _ = twomps.two_train_price(p)
         assert diags[0].status == tp.TT_OK
         assert abs(prices[0] / ref - 1) < 1e-4, (payoff, prices[0], ref)
+
+
+def test_invalid_problems_between_valid_ones(tp):
+    """A batch whose invalid problems (non-PD covariance, damping outside the strip)
+    sit between valid ones, in the two-train form with graph replay and plain
+    launches: the invalid ones get NaN and their status, and each valid problem's
+    bracket pairs its own two trains (its price equals its price alone)."""
+    good = [inputs.paper_table_problem(3).with_(seed=21 + i, n_grid=24, max_rank=8) for i in range(3)]
+    bad_pd = good[0].with_(cov=np.array([[1.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 1.0]]))
+    bad_strip = good[0].with_(damping=np.array([-0.2, -0.2, -0.2]))
+    batch = [good[0], bad_pd, good[1].with_(payoff="max"), bad_strip, good[2]]
+    for graph in (True, False):
+        rc, prices, diags = _price(tp, batch, "fp64", graph=graph)
+        assert [d.status for d in diags][1::2] == [tp.TT_ERR_NOT_PD, tp.TT_ERR_STRIP]
+        assert np.isnan(prices[1]) and np.isnan(prices[3])
+        for i in (0, 2, 4):
+            assert diags[i].status == tp.TT_OK
+            _, alone, _ = _price(tp, [batch[i]], "fp64", graph=graph)
+            assert prices[i] == alone[0], (i, prices[i], alone[0])
