@@ -30,8 +30,9 @@ Paper passages followed
     covariance A_j Cov A_j^T, so its characteristic function has the same form.
 
 Conventions (the readings used throughout the project)
-  * damping: the caller's ``damping[j]`` is the BASELINE-style alpha; the
-    imaginary shift is Im z_j = delta_j = -damping[j] for the min-call.  For the
+  * damping: the caller's ``damping[j]`` is alpha_j in the workloads' sign
+    convention (negative for the min-call); the imaginary shift is
+    Im z_j = delta_j = -damping[j] for the min-call.  For the
     max-call term j, delta_j = 1 + |damping[j]| on the maximum's axis and
     delta_l = -|damping[l]| on the others (so the aliasing rate on every axis is
     |damping|, as for the min-call).
