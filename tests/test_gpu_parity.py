@@ -243,8 +243,6 @@ def test_mixed_rank_tol_at_the_paper_setting(tp):
     """The paper's own setting (N=50, rank cap 15, d = 2, 5, 6): the default mixed
     rank threshold (1e-5) truncates below the cap there (3.3e-4 off the FP64 path
     at d = 6); with rank_tol = 1e-6 the mixed single train stays within 1e-4."""
-    from paper_2203_02804_gb300 import inputs
-
     probs = [inputs.paper_table_problem(2 + i % 5).with_(seed=1000 + i, max_rank=15)
              for i in (79, 84, 89, 94, 78, 83, 80, 85)]
     kw = dict(max_d=6, max_n=50, max_rank=15, max_batch=len(probs))
