@@ -342,7 +342,9 @@ def run_gpu(args):
     # launch configuration from the project's autotuner (untimed; measured on this GPU
     # for the workload's shape), else the library defaults
     tuned = {}
-    if not args.no_tune:
+    if args.engine != "auto":  # a fixed engine (profiling one engine); no tuning
+        tuned = {"engine": args.engine}
+    elif not args.no_tune:
         from paper_2203_02804_gb300 import autotune
 
         entry = autotune.tune(args.precision, 5, 128, 32, "min")
@@ -453,6 +455,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--engine", choices=["auto", "cuda", "tc"], default="auto",
+                    help="maxvol block-product engine; other than auto it replaces the autotuner's choice")
     ap.add_argument("--surrogate-samples", type=int, default=1 << 18,
                     help="TT-priced training samples of the learned surrogate (0: skip it)")
     ap.add_argument("--surrogate-epochs", type=int, default=40)
