@@ -9,8 +9,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
-#include <vector>
 
 #include "ttprice.h"
 #include "ttprice_device.cuh"
@@ -920,7 +920,12 @@ ttp::BrSmem make_brsmem(const tt_options& o, bool f64) {
 struct DevLayout {  // offsets inside the device workspace
   size_t stage, stage_bytes, jres, ires, counter, scratch, emit, emit_stride, total;
   size_t o_jobs, o_params, o_order, o_first, o_count, o_hstatus, o_pairs;  // inside the stage block
+  size_t o_host;  // host-only scratch of the preparation (never copied to the device)
 };
+
+// doubles of host scratch the preparation of one problem needs (d <= max_d):
+// a Cholesky factor and the derived per-axis vectors
+constexpr size_t host_scratch_doubles(size_t max_d) { return max_d * max_d + 8 * max_d; }
 
 DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   DevLayout D;
@@ -939,6 +944,7 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   D.o_hstatus = take(sizeof(int) * R.o.max_batch);
   const bool two = R.o.method == TT_METHOD_TWO_TRAINS;
   D.o_pairs = take(two ? sizeof(int2) * (size_t)R.max_jobs / 2 : 0);
+  D.o_host = take(sizeof(double) * host_scratch_doubles((size_t)R.o.max_d));
   D.stage_bytes = s;
   size_t off = 0;
   auto take2 = [&](size_t bytes) {
@@ -958,13 +964,44 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   return D;
 }
 
+// Dynamic shared memory above 48 KB needs a per-kernel opt-in, which is a
+// process-wide setting of the current device, shared by every pricer (and the
+// allocation-free entry point) that launches that kernel.  Pricers of different
+// sizes need different amounts, so the opt-in only ever rises: each launch path
+// raises it to at least its own need before it launches or replays a graph, and
+// a smaller pricer created later never lowers it under a larger one.
+constexpr int kMaxDevices = 64;
+std::mutex g_smem_mutex;
+
+template <typename K>
+cudaError_t raise_smem_optin(K* kernel, int* high, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_smem_mutex);
+  if (bytes <= high[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) high[dev] = bytes;
+  return e;
+}
+
+template <typename R, bool TC>
+cudaError_t cross_smem_optin(int bytes) {
+  static int high[kMaxDevices];
+  return raise_smem_optin(ttp::tt_cross_kernel<R, TC>, high, bytes);
+}
+
+cudaError_t bracket_smem_optin(int bytes) {
+  static int high[kMaxDevices];
+  return raise_smem_optin(ttp::bracket_kernel<double>, high, bytes);
+}
+
 // shared-memory opt-in and blocks per SM for one instantiation of the kernel
 template <typename R, bool TC>
 cudaError_t kernel_occupancy(const SmemLayout& S, int* per_sm, cudaFuncAttributes* fa) {
-  cudaError_t e = cudaFuncSetAttribute(ttp::tt_cross_kernel<R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       S.total);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(ttp::tt_cross_kernel<R, TC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaError_t e = cross_smem_optin<R, TC>(S.total);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ttp::tt_cross_kernel<R, TC>, ttp::kThreads, S.total);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(fa, ttp::tt_cross_kernel<R, TC>);
@@ -1014,8 +1051,10 @@ bool finite_all(const double* p, int n) {
   return true;
 }
 
-bool cholesky_ok(const double* c, int d) {
-  std::vector<double> l((size_t)d * d, 0.0);
+// FP64 Cholesky test of a symmetric matrix (the paper assumes a positive
+// definite covariance, Section II.A); l: d*d doubles of scratch
+bool cholesky_ok(const double* c, int d, double* l) {
+  for (int i = 0; i < d * d; ++i) l[i] = 0.0;
   double scale = 0.0;
   for (int i = 0; i < d * d; ++i) scale = std::max(scale, std::fabs(c[i]));
   for (int i = 0; i < d; ++i)
@@ -1065,6 +1104,216 @@ struct tt_pricer {
 
 namespace {
 
+// Validation of one problem (FP64, host); `scr` holds d*d doubles.  Returns
+// TT_OK or the problem's status.
+int validate_problem(const tt_problem& p, const tt_options& o, double* scr) {
+  const int d = p.d;
+  if (d < 1 || d > o.max_d || p.n_grid < 2 || p.n_grid > o.max_n || p.max_rank < 1 || p.max_rank > o.max_rank ||
+      !p.spot || !p.cov || !p.damping || (p.payoff != TT_MIN_CALL && p.payoff != TT_MAX_CALL))
+    return (d > o.max_d || p.n_grid > o.max_n || p.max_rank > o.max_rank) ? TT_ERR_CAPACITY : TT_ERR_INVALID;
+  if (!(p.trunc_L > 0) || !std::isfinite(p.trunc_L) || !(p.maturity > 0) || !std::isfinite(p.maturity) ||
+      !(p.strike > 0) || !std::isfinite(p.strike) || !std::isfinite(p.rate) || !finite_all(p.spot, d) ||
+      !finite_all(p.cov, d * d) || !finite_all(p.damping, d))
+    return TT_ERR_INVALID;
+  for (int j = 0; j < d; ++j)
+    if (!(p.spot[j] > 0)) return TT_ERR_INVALID;
+  if (!cholesky_ok(p.cov, d, scr)) return TT_ERR_NOT_PD;
+  if (p.payoff == TT_MIN_CALL) {
+    double sd = 0.0;
+    int stv = TT_OK;
+    for (int j = 0; j < d; ++j) {
+      if (!(-p.damping[j] > 0)) stv = TT_ERR_STRIP;
+      sd += -p.damping[j];
+    }
+    if (!(sd > 1.0)) stv = TT_ERR_STRIP;
+    return stv;
+  }
+  for (int j = 0; j < d; ++j)
+    if (!(std::fabs(p.damping[j]) > 0)) return TT_ERR_STRIP;
+  return TT_OK;
+}
+
+// Per-train derivation (Section III.C): covariance of the train's variables,
+// shifts delta, linear phase coefficients, log prefactor, sign and weight.
+// Writes the problem's jobs at jobs[nj..] and their parameter blocks at
+// params[poff..]; `scr` holds 8 d doubles.  No heap memory.
+void derive_trains(const tt_problem& p, int i, bool two, JobDesc* jobs, double* params, int2* pairs, int& nj,
+                   int& np, size_t& poff, int* cnt, double* scr) {
+  const int d = p.d;
+  const double T = p.maturity, K = p.strike, lk = std::log(K);
+  const int N = p.n_grid;
+  const double eta = 2.0 * p.trunc_L / N;
+  const double weight = std::exp(-p.rate * T) * std::pow(eta / (2.0 * M_PI), d);
+  double cap = 0.0;  // a call on the minimum or maximum is worth less than the sum of the spots
+  for (int j = 0; j < d; ++j) cap += p.spot[j];
+  double* m = scr;
+  for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
+  const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
+  auto base_job = [&](int term) {
+    JobDesc jd;
+    std::memset(&jd, 0, sizeof(jd));
+    jd.d = d;
+    jd.n = N;
+    jd.rmax = p.max_rank;
+    jd.instance = i;
+    jd.term = term;
+    jd.param_off = (int)poff;
+    jd.seed = p.seed;
+    jd.T = T;
+    jd.Tq = T;
+    jd.L = p.trunc_L;
+    jd.weight = weight;
+    jd.cap = cap;
+    return jd;
+  };
+  // covariance of max-call term j0's variables y_j0 = x_j0, y_l = x_l - x_j0: A Cov A^T
+  auto term_cov = [&](int j0, double* cv) {
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        double v = p.cov[a * d + b];
+        if (a != j0) v -= p.cov[j0 * d + b];
+        if (b != j0) v -= p.cov[a * d + j0];
+        if (a != j0 && b != j0) v += p.cov[j0 * d + j0];
+        cv[a * d + b] = v;
+      }
+  };
+  if (two) {
+    // Two-train form (Eq. braket): per term a payoff-transform train and a
+    // characteristic-function train, in the term's variables.  With mu_t the
+    // term's mean log-price vector, s the strike's direction (all ones for the
+    // min-call, e_j for max-call term j), delta the shift and C the covariance:
+    //   phi_T(-z) = exp(delta.mu_t + T/2 delta^T C delta) exp(-T/2 u^T C u)
+    //               * exp(-i u.(mu_t + T C delta)),
+    //   vhat(z)   = K^(1 - s.delta) e^{i ln K s.u} * (rational factors: 1/(i z_l),
+    //               1/((i z_j)(1 + i z_j)), and the min-call's 1/(1 + i sum z)).
+    const bool mn = p.payoff == TT_MIN_CALL;
+    double* dlv = m + d;
+    double* kdv = dlv + d;
+    double* mut = kdv + d;
+    double* sv = mut + d;
+    double* cd = sv + d;
+    for (int term = 0; term < terms; ++term) {
+      const int j0 = term;
+      // the term's covariance goes straight into the first factor's block
+      double* cv0 = params + poff;
+      if (mn) {
+        std::memcpy(cv0, p.cov, sizeof(double) * d * d);
+      } else {
+        term_cov(j0, cv0);
+      }
+      for (int l = 0; l < d; ++l) {
+        if (mn) {
+          dlv[l] = -p.damping[l];
+          kdv[l] = 0.0;
+          mut[l] = m[l] + lk;
+          sv[l] = 1.0;
+        } else {
+          dlv[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
+          kdv[l] = l == j0 ? 1.0 : 0.0;
+          mut[l] = l == j0 ? m[j0] + lk : m[l] - m[j0];
+          sv[l] = l == j0 ? 1.0 : 0.0;
+        }
+      }
+      double quad = 0.0, sdl = 0.0, dmu = 0.0;
+      for (int l = 0; l < d; ++l) {
+        double c = 0.0;
+        for (int q = 0; q < d; ++q) c += cv0[(size_t)l * d + q] * dlv[q];
+        cd[l] = c;
+        quad += dlv[l] * c;
+        sdl += dlv[l] * sv[l];
+        dmu += dlv[l] * mut[l];
+      }
+      pairs[np].x = nj;
+      pairs[np].y = nj + 1;
+      ++np;
+      for (int fi = 0; fi < 2; ++fi) {
+        const bool vh = fi == 0;
+        JobDesc jd = base_job(term);
+        jd.factor = vh ? ttp::FACTOR_VHAT : ttp::FACTOR_PHI;
+        jd.Tq = vh ? 0.0 : T;
+        double* cv = params + poff;
+        double* dl = cv + (size_t)d * d;
+        double* pc = dl + d;
+        double* kd = pc + d;
+        poff += (size_t)d * d + 3 * (size_t)d;
+        if (cv != cv0) std::memcpy(cv, cv0, sizeof(double) * d * d);
+        for (int l = 0; l < d; ++l) {
+          dl[l] = dlv[l];
+          pc[l] = vh ? -lk * sv[l] : mut[l] + T * cd[l];
+          kd[l] = vh ? kdv[l] : 2.0;
+        }
+        jd.cauchy = vh && mn ? 1 : 0;
+        jd.D0 = vh && mn ? 1.0 - sdl : 0.0;
+        jd.logscale = vh ? lk * (1.0 - sdl) : dmu + 0.5 * T * quad;
+        jd.sign = vh && mn && d % 2 == 0 ? -1.0 : 1.0;  // (-1)^(d+1) on the min-call's transform
+        jobs[nj++] = jd;
+        ++cnt[i];
+      }
+    }
+    return;
+  }
+  for (int term = 0; term < terms; ++term) {
+    JobDesc jd = base_job(term);
+    double* cv = params + poff;
+    double* dl = cv + (size_t)d * d;
+    double* pc = dl + d;
+    double* kd = pc + d;
+    poff += (size_t)d * d + 3 * (size_t)d;
+    if (p.payoff == TT_MIN_CALL) {
+      std::memcpy(cv, p.cov, sizeof(double) * d * d);
+      double sd = 0.0, dm = 0.0, quad = 0.0;
+      for (int j = 0; j < d; ++j) {
+        dl[j] = -p.damping[j];
+        sd += dl[j];
+        dm += dl[j] * m[j];
+        kd[j] = 0.0;
+      }
+      for (int j = 0; j < d; ++j) {
+        double c = 0.0;
+        for (int l = 0; l < d; ++l) c += p.cov[j * d + l] * dl[l];
+        pc[j] = m[j] + T * c;
+        quad += dl[j] * c;
+      }
+      jd.cauchy = 1;
+      jd.D0 = 1.0 - sd;
+      jd.logscale = lk + dm + 0.5 * T * quad;
+      jd.sign = (d % 2 == 1) ? 1.0 : -1.0;  // (-1)^(d+1)
+    } else {
+      // term `term`: y_term = x_term, y_l = x_l - x_term; C' = A Cov A^T
+      const int j0 = term;
+      term_cov(j0, cv);
+      double lsc = lk, quad = 0.0;
+      for (int l = 0; l < d; ++l) {
+        dl[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
+        kd[l] = l == j0 ? 1.0 : 0.0;
+      }
+      for (int l = 0; l < d; ++l) {
+        const double mp = l == j0 ? m[j0] : m[l] - m[j0];
+        double c = 0.0;
+        for (int q = 0; q < d; ++q) c += cv[l * d + q] * dl[q];
+        pc[l] = mp + T * c;
+        lsc += dl[l] * mp;
+        quad += dl[l] * c;
+      }
+      jd.cauchy = 0;
+      jd.D0 = 0.0;
+      jd.logscale = lsc + 0.5 * T * quad;
+      jd.sign = 1.0;
+    }
+    jobs[nj++] = jd;
+    ++cnt[i];
+  }
+}
+
+// Queue cost of a job (largest first): its fiber work d N r^2.
+double job_cost(const JobDesc& q) {
+  return (double)std::max(q.d - 1, 1) * q.n * (double)q.rmax * q.rmax * (q.d > 1 ? 1.0 : 0.01);
+}
+
+// A1 of the hot path: validate every problem, derive its trains into the
+// handle's host stage, order the jobs by cost, pack the used parts and make one
+// host-to-device copy.  Heap-free (the allocation-free entry point runs it on
+// its fixed arrays too).
 int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   const tt_options& o = h->R.o;
   if (count < 0 || count > o.max_batch || (count > 0 && !probs)) return TT_ERR_INVALID;
@@ -1076,225 +1325,22 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   int* cnt = reinterpret_cast<int*>(st + h->dl.o_count);
   int* hstat = reinterpret_cast<int*>(st + h->dl.o_hstatus);
   int2* pairs = reinterpret_cast<int2*>(st + h->dl.o_pairs);
+  double* scr = reinterpret_cast<double*>(st + h->dl.o_host);
   const bool two = o.method == TT_METHOD_TWO_TRAINS;
   int nj = 0, np = 0;
   size_t poff = 0;
-  std::vector<double> cost;
-  cost.reserve((size_t)count * 2);
   for (int i = 0; i < count; ++i) {
-    const tt_problem& p = probs[i];
     first[i] = nj;
     cnt[i] = 0;
-    hstat[i] = TT_OK;
-    const int d = p.d;
-    int stv = TT_OK;
-    if (d < 1 || d > o.max_d || p.n_grid < 2 || p.n_grid > o.max_n || p.max_rank < 1 ||
-        p.max_rank > o.max_rank || !p.spot || !p.cov || !p.damping ||
-        (p.payoff != TT_MIN_CALL && p.payoff != TT_MAX_CALL))
-      stv = (d > o.max_d || p.n_grid > o.max_n || p.max_rank > o.max_rank) ? TT_ERR_CAPACITY
-                                                                             : TT_ERR_INVALID;
-    else if (!(p.trunc_L > 0) || !std::isfinite(p.trunc_L) || !(p.maturity > 0) ||
-             !std::isfinite(p.maturity) || !(p.strike > 0) || !std::isfinite(p.strike) ||
-             !std::isfinite(p.rate) || !finite_all(p.spot, d) || !finite_all(p.cov, d * d) ||
-             !finite_all(p.damping, d))
-      stv = TT_ERR_INVALID;
-    else {
-      for (int j = 0; j < d; ++j)
-        if (!(p.spot[j] > 0)) stv = TT_ERR_INVALID;
-      if (stv == TT_OK && !cholesky_ok(p.cov, d)) stv = TT_ERR_NOT_PD;
-      if (stv == TT_OK) {
-        if (p.payoff == TT_MIN_CALL) {
-          double sd = 0.0;
-          for (int j = 0; j < d; ++j) {
-            if (!(-p.damping[j] > 0)) stv = TT_ERR_STRIP;
-            sd += -p.damping[j];
-          }
-          if (!(sd > 1.0)) stv = TT_ERR_STRIP;
-        } else {
-          for (int j = 0; j < d; ++j)
-            if (!(std::fabs(p.damping[j]) > 0)) stv = TT_ERR_STRIP;
-        }
-      }
-    }
-    if (stv != TT_OK) {
-      hstat[i] = stv;
-      continue;
-    }
-    const double T = p.maturity, K = p.strike, lk = std::log(K);
-    const int N = p.n_grid;
-    const double eta = 2.0 * p.trunc_L / N;
-    const double weight = std::exp(-p.rate * T) * std::pow(eta / (2.0 * M_PI), d);
-    double cap = 0.0;  // a call on the minimum or maximum is worth less than the sum of the spots
-    for (int j = 0; j < d; ++j) cap += p.spot[j];
-    std::vector<double> m(d);
-    for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
-    const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
-    if (two) {
-      // Two-train form (Eq. braket): per term a payoff-transform train and a
-      // characteristic-function train, in the term's variables.  With mu_t the
-      // term's mean log-price vector, s the strike's direction (all ones for the
-      // min-call, e_j for max-call term j), delta the shift and C the covariance:
-      //   phi_T(-z) = exp(delta.mu_t + T/2 delta^T C delta) exp(-T/2 u^T C u)
-      //               * exp(-i u.(mu_t + T C delta)),
-      //   vhat(z)   = K^(1 - s.delta) e^{i ln K s.u} * (rational factors: 1/(i z_l),
-      //               1/((i z_j)(1 + i z_j)), and the min-call's 1/(1 + i sum z)).
-      const bool mn = p.payoff == TT_MIN_CALL;
-      std::vector<double> cvv((size_t)d * d), dlv(d), kdv(d), mut(d), sv(d), cd(d);
-      for (int term = 0; term < terms; ++term) {
-        const int j0 = term;
-        for (int a = 0; a < d; ++a)
-          for (int b = 0; b < d; ++b) {
-            auto cov = [&](int r, int c) { return p.cov[r * d + c]; };
-            double v = cov(a, b);
-            if (!mn) {
-              if (a != j0) v -= cov(j0, b);
-              if (b != j0) v -= cov(a, j0);
-              if (a != j0 && b != j0) v += cov(j0, j0);
-            }
-            cvv[(size_t)a * d + b] = v;
-          }
-        for (int l = 0; l < d; ++l) {
-          if (mn) {
-            dlv[l] = -p.damping[l];
-            kdv[l] = 0.0;
-            mut[l] = m[l] + lk;
-            sv[l] = 1.0;
-          } else {
-            dlv[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
-            kdv[l] = l == j0 ? 1.0 : 0.0;
-            mut[l] = l == j0 ? m[j0] + lk : m[l] - m[j0];
-            sv[l] = l == j0 ? 1.0 : 0.0;
-          }
-        }
-        double quad = 0.0, sdl = 0.0, dmu = 0.0;
-        for (int l = 0; l < d; ++l) {
-          double c = 0.0;
-          for (int q = 0; q < d; ++q) c += cvv[(size_t)l * d + q] * dlv[q];
-          cd[l] = c;
-          quad += dlv[l] * c;
-          sdl += dlv[l] * sv[l];
-          dmu += dlv[l] * mut[l];
-        }
-        pairs[np].x = nj;
-        pairs[np].y = nj + 1;
-        ++np;
-        for (int fi = 0; fi < 2; ++fi) {
-          const bool vh = fi == 0;
-          JobDesc jd;
-          std::memset(&jd, 0, sizeof(jd));
-          jd.d = d;
-          jd.n = N;
-          jd.rmax = p.max_rank;
-          jd.instance = i;
-          jd.term = term;
-          jd.param_off = (int)poff;
-          jd.factor = vh ? ttp::FACTOR_VHAT : ttp::FACTOR_PHI;
-          jd.seed = p.seed;
-          jd.T = T;
-          jd.Tq = vh ? 0.0 : T;
-          jd.L = p.trunc_L;
-          jd.weight = weight;
-          jd.cap = cap;
-          double* cv = params + poff;
-          double* dl = cv + (size_t)d * d;
-          double* pc = dl + d;
-          double* kd = pc + d;
-          poff += (size_t)d * d + 3 * (size_t)d;
-          std::memcpy(cv, cvv.data(), sizeof(double) * d * d);
-          for (int l = 0; l < d; ++l) {
-            dl[l] = dlv[l];
-            pc[l] = vh ? -lk * sv[l] : mut[l] + T * cd[l];
-            kd[l] = vh ? kdv[l] : 2.0;
-          }
-          jd.cauchy = vh && mn ? 1 : 0;
-          jd.D0 = vh && mn ? 1.0 - sdl : 0.0;
-          jd.logscale = vh ? lk * (1.0 - sdl) : dmu + 0.5 * T * quad;
-          jd.sign = vh && mn && d % 2 == 0 ? -1.0 : 1.0;  // (-1)^(d+1) on the min-call's transform
-          jobs[nj] = jd;
-          cost.push_back((double)std::max(d - 1, 1) * N * (double)p.max_rank * p.max_rank * (d > 1 ? 1.0 : 0.01));
-          ++nj;
-          ++cnt[i];
-        }
-      }
-      continue;
-    }
-    for (int term = 0; term < terms; ++term) {
-      JobDesc jd;
-      std::memset(&jd, 0, sizeof(jd));
-      jd.d = d;
-      jd.n = N;
-      jd.rmax = p.max_rank;
-      jd.instance = i;
-      jd.term = term;
-      jd.param_off = (int)poff;
-      jd.seed = p.seed;
-      jd.T = T;
-      jd.Tq = T;
-      jd.L = p.trunc_L;
-      jd.weight = weight;
-      jd.cap = cap;
-      double* cv = params + poff;
-      double* dl = cv + (size_t)d * d;
-      double* pc = dl + d;
-      double* kd = pc + d;
-      poff += (size_t)d * d + 3 * (size_t)d;
-      if (p.payoff == TT_MIN_CALL) {
-        std::memcpy(cv, p.cov, sizeof(double) * d * d);
-        double sd = 0.0, dm = 0.0, quad = 0.0;
-        for (int j = 0; j < d; ++j) {
-          dl[j] = -p.damping[j];
-          sd += dl[j];
-          dm += dl[j] * m[j];
-          kd[j] = 0.0;
-        }
-        for (int j = 0; j < d; ++j) {
-          double cd = 0.0;
-          for (int l = 0; l < d; ++l) cd += p.cov[j * d + l] * dl[l];
-          pc[j] = m[j] + T * cd;
-          quad += dl[j] * cd;
-        }
-        jd.cauchy = 1;
-        jd.D0 = 1.0 - sd;
-        jd.logscale = lk + dm + 0.5 * T * quad;
-        jd.sign = (d % 2 == 1) ? 1.0 : -1.0;  // (-1)^(d+1)
-      } else {
-        // term `term`: y_term = x_term, y_l = x_l - x_term; C' = A Cov A^T
-        const int j0 = term;
-        for (int a = 0; a < d; ++a)
-          for (int b = 0; b < d; ++b) {
-            auto cov = [&](int r, int c) { return p.cov[r * d + c]; };
-            double v = cov(a, b);
-            if (a != j0) v -= cov(j0, b);
-            if (b != j0) v -= cov(a, j0);
-            if (a != j0 && b != j0) v += cov(j0, j0);
-            cv[a * d + b] = v;
-          }
-        double lsc = lk, quad = 0.0;
-        for (int l = 0; l < d; ++l) {
-          dl[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
-          kd[l] = l == j0 ? 1.0 : 0.0;
-        }
-        for (int l = 0; l < d; ++l) {
-          const double mp = l == j0 ? m[j0] : m[l] - m[j0];
-          double cd = 0.0;
-          for (int q = 0; q < d; ++q) cd += cv[l * d + q] * dl[q];
-          pc[l] = mp + T * cd;
-          lsc += dl[l] * mp;
-          quad += dl[l] * cd;
-        }
-        jd.cauchy = 0;
-        jd.D0 = 0.0;
-        jd.logscale = lsc + 0.5 * T * quad;
-        jd.sign = 1.0;
-      }
-      jobs[nj] = jd;
-      cost.push_back((double)std::max(d - 1, 1) * N * (double)p.max_rank * p.max_rank * (d > 1 ? 1.0 : 0.01));
-      ++nj;
-      ++cnt[i];
-    }
+    hstat[i] = validate_problem(probs[i], o, scr);
+    if (hstat[i] == TT_OK) derive_trains(probs[i], i, two, jobs, params, pairs, nj, np, poff, cnt, scr);
   }
+  // largest jobs first, ties by job number (std::sort works in place)
   for (int j = 0; j < nj; ++j) order[j] = j;
-  std::stable_sort(order, order + nj, [&](int a, int b) { return cost[a] > cost[b]; });
+  std::sort(order, order + nj, [&](int a, int b) {
+    const double ca = job_cost(jobs[a]), cb = job_cost(jobs[b]);
+    return ca != cb ? ca > cb : a < b;
+  });
   h->count = count;
   h->njobs = nj;
   h->npairs = np;
@@ -1367,9 +1413,25 @@ int launch_all(tt_pricer* h, cudaStream_t stream) {
   return TT_OK;
 }
 
+// the shared-memory opt-in of every kernel this pricer launches (see raise_smem_optin)
+int ensure_smem_optin(const tt_pricer* h) {
+  cudaError_t e = h->R.o.precision == TT_FP64 ? cross_smem_optin<double, false>(h->sml.total)
+                  : h->R.o.engine == TT_ENGINE_TENSOR_CORES ? cross_smem_optin<float, true>(h->sml.total)
+                                                            : cross_smem_optin<float, false>(h->sml.total);
+  if (e == cudaSuccess && h->R.o.method == TT_METHOD_TWO_TRAINS) e = bracket_smem_optin(h->bsm.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TT_ERR_CUDA;
+  }
+  return TT_OK;
+}
+
 // graph replay: re-captured whenever the batch layout (job and problem counts,
 // packed offsets) differs from the captured one
 int run_impl(tt_pricer* h) {
+  // before any launch, capture or replay (no attribute call inside a capture)
+  const int orc = ensure_smem_optin(h);
+  if (orc != TT_OK) return orc;
   if (!h->R.o.graph) return launch_all(h, h->stream);
   const size_t key[8] = {(size_t)h->njobs, (size_t)h->count, h->p_jobs, h->p_params,
                          h->p_order, h->p_first, h->p_count, h->p_hstatus ^ (h->p_pairs << 32) ^ (size_t)h->npairs};
@@ -1475,8 +1537,7 @@ int tt_price_create(const tt_options* opt, tt_pricer** out) {
   h->bsm = ttp::BrSmem{};
   if (R.o.method == TT_METHOD_TWO_TRAINS) {
     h->bsm = make_brsmem(R.o, true);
-    const cudaError_t e = cudaFuncSetAttribute(ttp::bracket_kernel<double>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, h->bsm.total);
+    const cudaError_t e = bracket_smem_optin(h->bsm.total);
     if (h->bsm.total > 227 * 1024 || e != cudaSuccess) {
       cudaGetLastError();
       delete h;
@@ -1620,7 +1681,8 @@ constexpr int kStaticJobs = TT_STATIC_MAX_BATCH * TT_STATIC_MAX_D;
 constexpr size_t kStaticParams = (size_t)kStaticJobs * (TT_STATIC_MAX_D * TT_STATIC_MAX_D + 3 * TT_STATIC_MAX_D);
 constexpr size_t kStaticStageBytes =
     (sizeof(JobDesc) * kStaticJobs + 255) / 256 * 256 + (sizeof(double) * kStaticParams + 255) / 256 * 256 +
-    (sizeof(int) * kStaticJobs + 255) / 256 * 256 + 3 * ((sizeof(int) * TT_STATIC_MAX_BATCH + 255) / 256 * 256);
+    (sizeof(int) * kStaticJobs + 255) / 256 * 256 + 3 * ((sizeof(int) * TT_STATIC_MAX_BATCH + 255) / 256 * 256) +
+    (sizeof(double) * host_scratch_doubles(TT_STATIC_MAX_D) + 255) / 256 * 256;
 constexpr int kStaticMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[TT_STATIC_SCRATCH_BYTES];
@@ -1647,196 +1709,6 @@ tt_options static_options(int precision, int device, void* stream) {
   o.device = device;
   o.cuda_stream = stream;
   return o;
-}
-
-// Cholesky test without heap memory (d <= TT_STATIC_MAX_D)
-bool cholesky_ok_small(const double* c, int d) {
-  double l[TT_STATIC_MAX_D * TT_STATIC_MAX_D] = {0.0};
-  double scale = 0.0;
-  for (int i = 0; i < d * d; ++i) scale = std::max(scale, std::fabs(c[i]));
-  for (int i = 0; i < d; ++i)
-    for (int j = 0; j < i; ++j)
-      if (std::fabs(c[i * d + j] - c[j * d + i]) > 1e-12 * scale) return false;
-  for (int j = 0; j < d; ++j) {
-    double s = c[j * d + j];
-    for (int k = 0; k < j; ++k) s -= l[j * d + k] * l[j * d + k];
-    if (!(s > 0.0)) return false;
-    const double ljj = std::sqrt(s);
-    l[j * d + j] = ljj;
-    for (int i = j + 1; i < d; ++i) {
-      double t = c[i * d + j];
-      for (int k = 0; k < j; ++k) t -= l[i * d + k] * l[j * d + k];
-      l[i * d + j] = t / ljj;
-    }
-  }
-  return true;
-}
-
-// Validation and per-train derivation into the handle's host stage, with no
-// heap use (fixed arrays, in-place sort); same rules and formulas as the
-// handle-based preparation.
-int prepare_static(tt_pricer* h, const tt_problem* probs, int count) {
-  const tt_options& o = h->R.o;
-  char* st = h->h_stage;
-  JobDesc* jobs = reinterpret_cast<JobDesc*>(st + h->dl.o_jobs);
-  double* params = reinterpret_cast<double*>(st + h->dl.o_params);
-  int* order = reinterpret_cast<int*>(st + h->dl.o_order);
-  int* first = reinterpret_cast<int*>(st + h->dl.o_first);
-  int* cnt = reinterpret_cast<int*>(st + h->dl.o_count);
-  int* hstat = reinterpret_cast<int*>(st + h->dl.o_hstatus);
-  int nj = 0;
-  size_t poff = 0;
-  for (int i = 0; i < count; ++i) {
-    const tt_problem& p = probs[i];
-    first[i] = nj;
-    cnt[i] = 0;
-    hstat[i] = TT_OK;
-    const int d = p.d;
-    int stv = TT_OK;
-    if (d < 1 || d > o.max_d || p.n_grid < 2 || p.n_grid > o.max_n || p.max_rank < 1 ||
-        p.max_rank > o.max_rank || !p.spot || !p.cov || !p.damping ||
-        (p.payoff != TT_MIN_CALL && p.payoff != TT_MAX_CALL))
-      stv = (d > o.max_d || p.n_grid > o.max_n || p.max_rank > o.max_rank) ? TT_ERR_CAPACITY
-                                                                             : TT_ERR_INVALID;
-    else if (!(p.trunc_L > 0) || !std::isfinite(p.trunc_L) || !(p.maturity > 0) ||
-             !std::isfinite(p.maturity) || !(p.strike > 0) || !std::isfinite(p.strike) ||
-             !std::isfinite(p.rate) || !finite_all(p.spot, d) || !finite_all(p.cov, d * d) ||
-             !finite_all(p.damping, d))
-      stv = TT_ERR_INVALID;
-    else {
-      for (int j = 0; j < d; ++j)
-        if (!(p.spot[j] > 0)) stv = TT_ERR_INVALID;
-      if (stv == TT_OK && !cholesky_ok_small(p.cov, d)) stv = TT_ERR_NOT_PD;
-      if (stv == TT_OK) {
-        if (p.payoff == TT_MIN_CALL) {
-          double sd = 0.0;
-          for (int j = 0; j < d; ++j) {
-            if (!(-p.damping[j] > 0)) stv = TT_ERR_STRIP;
-            sd += -p.damping[j];
-          }
-          if (!(sd > 1.0)) stv = TT_ERR_STRIP;
-        } else {
-          for (int j = 0; j < d; ++j)
-            if (!(std::fabs(p.damping[j]) > 0)) stv = TT_ERR_STRIP;
-        }
-      }
-    }
-    if (stv != TT_OK) {
-      hstat[i] = stv;
-      continue;
-    }
-    const double T = p.maturity, K = p.strike, lk = std::log(K);
-    const int N = p.n_grid;
-    const double eta = 2.0 * p.trunc_L / N;
-    const double weight = std::exp(-p.rate * T) * std::pow(eta / (2.0 * M_PI), d);
-    double cap = 0.0;  // a call on the minimum or maximum is worth less than the sum of the spots
-    for (int j = 0; j < d; ++j) cap += p.spot[j];
-    double m[TT_STATIC_MAX_D];
-    for (int j = 0; j < d; ++j) m[j] = std::log(p.spot[j] / K) + (p.rate - 0.5 * p.cov[j * d + j]) * T;
-    const int terms = p.payoff == TT_MIN_CALL ? 1 : d;
-    for (int term = 0; term < terms; ++term) {
-      JobDesc jd;
-      std::memset(&jd, 0, sizeof(jd));
-      jd.d = d;
-      jd.n = N;
-      jd.rmax = p.max_rank;
-      jd.instance = i;
-      jd.term = term;
-      jd.param_off = (int)poff;
-      jd.seed = p.seed;
-      jd.T = T;
-      jd.Tq = T;
-      jd.L = p.trunc_L;
-      jd.weight = weight;
-      jd.cap = cap;
-      double* cv = params + poff;
-      double* dl = cv + (size_t)d * d;
-      double* pc = dl + d;
-      double* kd = pc + d;
-      poff += (size_t)d * d + 3 * (size_t)d;
-      if (p.payoff == TT_MIN_CALL) {
-        std::memcpy(cv, p.cov, sizeof(double) * d * d);
-        double sd = 0.0, dm = 0.0, quad = 0.0;
-        for (int j = 0; j < d; ++j) {
-          dl[j] = -p.damping[j];
-          sd += dl[j];
-          dm += dl[j] * m[j];
-          kd[j] = 0.0;
-        }
-        for (int j = 0; j < d; ++j) {
-          double cd = 0.0;
-          for (int l = 0; l < d; ++l) cd += p.cov[j * d + l] * dl[l];
-          pc[j] = m[j] + T * cd;
-          quad += dl[j] * cd;
-        }
-        jd.cauchy = 1;
-        jd.D0 = 1.0 - sd;
-        jd.logscale = lk + dm + 0.5 * T * quad;
-        jd.sign = (d % 2 == 1) ? 1.0 : -1.0;
-      } else {
-        const int j0 = term;
-        for (int a = 0; a < d; ++a)
-          for (int b = 0; b < d; ++b) {
-            double v = p.cov[a * d + b];
-            if (a != j0) v -= p.cov[j0 * d + b];
-            if (b != j0) v -= p.cov[a * d + j0];
-            if (a != j0 && b != j0) v += p.cov[j0 * d + j0];
-            cv[a * d + b] = v;
-          }
-        double lsc = lk, quad = 0.0;
-        for (int l = 0; l < d; ++l) {
-          dl[l] = l == j0 ? 1.0 + std::fabs(p.damping[l]) : -std::fabs(p.damping[l]);
-          kd[l] = l == j0 ? 1.0 : 0.0;
-        }
-        for (int l = 0; l < d; ++l) {
-          const double mp = l == j0 ? m[j0] : m[l] - m[j0];
-          double cd = 0.0;
-          for (int q = 0; q < d; ++q) cd += cv[l * d + q] * dl[q];
-          pc[l] = mp + T * cd;
-          lsc += dl[l] * mp;
-          quad += dl[l] * cd;
-        }
-        jd.cauchy = 0;
-        jd.D0 = 0.0;
-        jd.logscale = lsc + 0.5 * T * quad;
-        jd.sign = 1.0;
-      }
-      jobs[nj] = jd;
-      ++nj;
-      ++cnt[i];
-    }
-  }
-  // largest jobs first; ties by job number (std::sort works in place)
-  auto cost = [&](int j) {
-    const JobDesc& q = jobs[j];
-    return (double)std::max(q.d - 1, 1) * q.n * (double)q.rmax * q.rmax * (q.d > 1 ? 1.0 : 0.01);
-  };
-  for (int j = 0; j < nj; ++j) order[j] = j;
-  std::sort(order, order + nj, [&](int a, int b) {
-    const double ca = cost(a), cb = cost(b);
-    return ca != cb ? ca > cb : a < b;
-  });
-  h->count = count;
-  h->njobs = nj;
-  size_t off = 0;
-  auto put = [&](size_t src_off, size_t bytes) {
-    const size_t at = off;
-    if (bytes) std::memcpy(h->h_pack + at, h->h_stage + src_off, bytes);
-    off = align_up(off + bytes, 16);
-    return at;
-  };
-  h->p_jobs = put(h->dl.o_jobs, sizeof(JobDesc) * nj);
-  h->p_params = put(h->dl.o_params, sizeof(double) * poff);
-  h->p_order = put(h->dl.o_order, sizeof(int) * nj);
-  h->p_first = put(h->dl.o_first, sizeof(int) * count);
-  h->p_count = put(h->dl.o_count, sizeof(int) * count);
-  h->p_hstatus = put(h->dl.o_hstatus, sizeof(int) * count);
-  h->p_bytes = off;
-  h->last_h2d = off;
-  if (off && cudaMemcpyAsync(h->ws + h->dl.stage, h->h_pack, off, cudaMemcpyHostToDevice,
-                             h->stream) != cudaSuccess)
-    return TT_ERR_CUDA;
-  return TT_OK;
 }
 
 // One-time set-up per device (with that device current): the array's device
@@ -1903,7 +1775,7 @@ extern "C" int tt_price_evaluate_static(const tt_problem* probs, int count, int 
   h.npairs = 0;
   h.p_pairs = 0;
   h.last_h2d = h.last_d2h = 0;
-  rc = prepare_static(&h, probs, count);
+  rc = prepare_impl(&h, probs, count);
   if (rc != TT_OK) return rc;
   rc = run_impl(&h);
   if (rc != TT_OK) return rc;
