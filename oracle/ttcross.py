@@ -2,46 +2,50 @@
 
 Test infrastructure only (see the package docstring).
 
-What the paper fixes (Section IV.A-B) and what is read into it
+The algorithm, in the paper's order (Section IV.B)
   * The integrand tensor is approximated by a tensor train (matrix product
-    state) built from actual tensor entries by TT-cross: sweep back and forth
-    over the cores; at each core solve a matrix cross problem M ~ M(:,J)
-    M(I,J)^{-1} M(I,:) with the other index sets fixed, choosing the rows I of
-    (quasi-)maximal volume by maxvol, starting from random column sets J.
-  * The paper leaves the details to its references.  The readings used here,
-    and implemented independently by the CUDA library:
-      - core k's fiber matrix A has rows (outer multi-index o, grid index i),
-        row number o*N + i, and the opposite index set as columns;
-      - initial rows: Gaussian elimination with partial pivoting (GEPP) run as a
-        flat tournament: the current winners are stacked on top of the next
-        candidates and GEPP keeps the pivot rows.  Candidates are the next block
-        of ``block_rows`` rows for fibers of at most 512 rows; larger fibers are
-        screened in blocks of 1024 rows, each 128-row sub-block offering its 16
-        rows with the largest entries.  A column whose best pivot is at most
-        ``theta`` times that column's largest entry is skipped (numerically
-        dependent); the pivot block of the winners then drops the columns
-        whose block entries are at most theta times their largest fiber entry,
-        and is reduced by complete pivoting on its column-equilibrated entries
-        (stop at theta), which keeps its condition number near 1/theta; the
-        kept columns set the rank;
-      - maxvol: B = A_c A_c[W]^{-1} on the kept columns, blocks visited
-        cyclically; inside a block, while max |B_ij| > 1 + tau swap row i into
-        slot j (rank-one update of B, at most rank-many swaps per block); stop
-        after every block has been visited once with no swap (then
-        |B| <= 1 + tau on the whole matrix) or after 4 * n_blocks visits;
-      - the interpolation core is G = A_c A_c[W]^{-1}; its sum over the grid
-        index is what the contraction with the quadrature weights needs;
-      - half-sweeps alternate left-to-right / right-to-left; each ends with a
-        price estimate and the sweep stops when two consecutive estimates agree
-        to ``sweep_tol`` (relative), or after ``max_half_sweeps``;
-      - ranks r_k = min(r_max, N^k, N^(d-k)); initial right sets draw distinct
-        multi-indices with SplitMix64 around the grid centre, with a spread of
-        1.5 standard deviations of the integrand's Gaussian factor per axis
-        (slot 0 is the centre), or list all N^(d-k) of them in lexicographic
-        order when r_k = N^(d-k).
+    state) built from actual tensor entries.  Sweeping back and forth over the
+    cores with the other index sets fixed, each core solves one matrix cross
+    problem M ~ M(:,J) M(I,J)^{-1} M(I,:): starting from the column set J (at
+    first random), it takes the r rows of (quasi-)maximal volume in M(:,J) by
+    maxvol; those rows are the next core's row index set, and the sweep in the
+    other direction does the same for the columns.
+  * maxvol (Goreinov-Tyrtyshnikov, the paper's maxvol reference): start from r
+    rows with a non-singular r x r block (Gaussian elimination with partial
+    pivoting, the usual start), form B = A A[I]^{-1} over all rows of the fiber,
+    and while some |B_ij| > 1 + tau swap row i into slot j (a rank-one update
+    of B; every swap multiplies |det A[I]| by |B_ij|).  It stops with
+    |B| <= 1 + tau on the whole fiber.  As in the TT-cross references the paper
+    cites, maxvol runs on an orthonormal basis of the fiber's columns (QR):
+    B, and hence the rows, are the same for any basis of the same column span.
+  * Convergence: the paper checks a sampled one-norm after each sweep; here
+    each half-sweep ends with the estimate of the weighted sum it computes,
+    and the sweeps stop when two consecutive estimates agree to ``sweep_tol``
+    (relative) or after ``max_half_sweeps``.
   * Contraction (Section IV.A, MPS inner product): the weights are eta per axis
     (folded into the tensor's scale), so the weighted sum of the train is the
-    product of the per-core sums W_k = sum_i G_k[:, i, :].
+    product of the per-core sums W_k = sum_i G_k[:, i, :] of the interpolation
+    cores G_k = A_k A_k[I_k]^{-1}.
+
+Readings where the paper leaves details to its references
+  * Core k's fiber matrix has rows (outer multi-index o, grid index i), row
+    number o*N + i, and the opposite index set as columns.
+  * Rank: the paper fixes the bond dimension D.  Where the fiber matrix has
+    numerical rank below its column count, A[I] would be singular.  The QR is
+    therefore column-pivoted (rank revealing): the rank r_k is the count of
+    |R_kk| > theta |R_00| and the first r_k pivot columns are kept.  Ranks start
+    at r_k = min(D, N^k, N^(d-k)) and can only fall.
+  * Column scaling: every fiber column is scaled by a power of two that brings
+    its largest entry near one, before the QR.  It equilibrates the columns
+    for the rank decision (the column-pivoted QR compares column norms) and
+    keeps |a|^2 inside the FP64 range for fibers through far tails; maxvol's B
+    and the interpolation core are invariant under it.
+  * Initial column sets: distinct multi-indices drawn with SplitMix64 around
+    the grid centre, with a spread of 1.5 standard deviations of the
+    integrand's Gaussian factor per axis (slot 0 is the centre), or all
+    N^(d-k) of them in lexicographic order when r_k = N^(d-k).
+  * maxvol's tolerance tau (0.05) and a swap cap of 100 r per core (never
+    reached in the tests; reaching it is reported in the diagnostics).
 """
 from __future__ import annotations
 
@@ -49,17 +53,18 @@ import math
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.linalg
 
 from .splitmix import pivot_key, splitmix64
 
 
 @dataclass
 class CrossOptions:
-    block_rows: int = 128
     theta: float = 1e-8           # relative pivot threshold for skipping a column
     tau: float = 0.05             # maxvol tolerance: stop when |B| <= 1 + tau
     max_half_sweeps: int = 8
     sweep_tol: float = 1e-6
+    swap_cap: int = 100           # maxvol swaps per core at most swap_cap * rank
 
 
 @dataclass
@@ -144,7 +149,7 @@ def initial_right_set(d, n, k, size, seed, term, widths=None):
 
 
 # ----------------------------------------------------------------------------
-# row selection: GEPP tournament and maxvol
+# row selection: elimination start and maxvol
 # ----------------------------------------------------------------------------
 
 def gepp_select(c_mat, theta):
@@ -179,123 +184,28 @@ def gepp_select(c_mat, theta):
     return rows, cols
 
 
-SCREEN_MIN_ROWS = 512   # fibers with more rows than this are screened
-SCREEN_BLOCK = 1024     # rows per screening block (one GEPP merge each)
-SCREEN_SUB = 128        # rows per sub-block
-SCREEN_KEEP = 16        # rows each sub-block keeps (a fiber of more than 512 rows offers >= 64)
+def maxvol(a_cols, rows, tau, max_swaps):
+    """maxvol on the whole tall matrix ``a_cols`` (m x r), starting from ``rows``.
 
-
-def screen_rows(a_mat, start, stop):
-    """Candidates of one screening block: in every 128-row sub-block, the 16 rows
-    whose largest |entry|^2 (over all columns, rounded to FP32) is largest, ties
-    to the lower row; returned in ascending row order."""
-    keys = (a_mat[start:stop].real ** 2 + a_mat[start:stop].imag ** 2).max(axis=1).astype(np.float32)
-    kept = []
-    for s0 in range(0, stop - start, SCREEN_SUB):
-        sub = list(range(s0, min(stop - start, s0 + SCREEN_SUB)))
-        best = sorted(sub, key=lambda r: (-float(keys[r]), r))[:SCREEN_KEEP]
-        kept += [start + r for r in sorted(best)]
-    return kept
-
-
-def tournament_select(a_mat, block_rows, theta, screen_mat=None):
-    """Flat GEPP tournament; returns (winner rows, kept columns).
-
-    Each merge runs GEPP on the current winners stacked on top of new
-    candidates: the next block of ``block_rows`` rows when the fiber has at most
-    SCREEN_MIN_ROWS rows, else the screened rows of the next SCREEN_BLOCK rows
-    (screening keys from ``screen_mat``, default ``a_mat``).
+    B = A A[rows]^{-1}; while max |B_ij| > 1 + tau: row i replaces slot j and B
+    takes the rank-one update B -= B[:, j] (B[i, :] - e_j) / B[i, j].  Returns
+    (rows, swaps, converged); converged means |B| <= 1 + tau everywhere.
     """
-    m = a_mat.shape[0]
-    keys_from = a_mat if screen_mat is None else screen_mat
-    winners, cols = [], []
-    step = block_rows if m <= SCREEN_MIN_ROWS else SCREEN_BLOCK
-    for start in range(0, m, step):
-        stop = min(m, start + step)
-        fresh = list(range(start, stop)) if m <= SCREEN_MIN_ROWS else screen_rows(keys_from, start, stop)
-        cand = winners + fresh
-        r, c = gepp_select(a_mat[cand, :], theta)
-        winners = [cand[p] for p in r]
-        cols = c
-    return winners, cols
-
-
-def rank_reveal(p_mat, theta, col_ref=None):
-    """Rank-revealing reduction of the pivot block; returns (rows, cols) in pivot order.
-
-    1. A column whose largest |entry|^2 in the block is at most theta^2 times
-       ``col_ref`` (its largest |entry|^2 over the whole fiber column) is
-       numerically absent from the block and is dropped.
-    2. Gaussian elimination with complete pivoting on the column-equilibrated
-       block: every entry's |.|^2 is divided by its column's largest in the
-       block, at every step the largest such value of the remaining block
-       (first in row-major order on ties) is the pivot, and the reduction stops
-       when it is at most theta^2.
-    Both rules are invariant under column scaling, as the interpolation is; the
-    kept sub-block has condition number about 1/theta after column
-    equilibration, which the tournament's partial pivoting alone does not
-    guarantee."""
-    s = np.array(p_mat, dtype=np.complex128, copy=True)
-    q, n = s.shape
-    blockmax = (s.real ** 2 + s.imag ** 2).max(axis=0)
-    keep = blockmax > 0
-    if col_ref is not None:
-        keep &= blockmax > theta * theta * np.asarray(col_ref, dtype=np.float64)
-    scale = np.where(keep, blockmax, np.inf)  # a dropped column never pivots
-    free_r = np.ones(q, dtype=bool)
-    free_c = np.ones(n, dtype=bool)
-    rows, cols = [], []
-    while free_r.any() and free_c.any():
-        mag = (s.real ** 2 + s.imag ** 2) / scale[None, :]
-        mag[~free_r, :] = -1.0
-        mag[:, ~free_c] = -1.0
-        p, c = divmod(int(np.argmax(mag)), n)
-        if not (mag[p, c] > theta * theta):
-            break
-        rows.append(p)
-        cols.append(c)
-        free_r[p] = False
-        free_c[c] = False
-        mult = s[:, c] / s[p, c]
-        mult[~free_r] = 0.0
-        s -= np.outer(mult, s[p, :])
-    return rows, cols
-
-
-def maxvol_refine(a_cols, rows, block_rows, tau):
-    """Cyclic block maxvol on the kept columns, starting from ``rows``.
-
-    Returns (rows, swaps, converged).
-    """
-    m, rho = a_cols.shape
     rows = list(rows)
-    nb = -(-m // block_rows)
-    thr = (1.0 + tau) ** 2
-    quiet = visits = swaps = 0
-    beta = 0
-    while quiet < nb and visits < 4 * nb:
-        blk = list(range(beta * block_rows, min(m, (beta + 1) * block_rows)))
-        inv = np.linalg.inv(a_cols[rows, :])
-        b_mat = a_cols[blk, :] @ inv
-        swapped = False
-        for _ in range(rho):
-            mag = b_mat.real ** 2 + b_mat.imag ** 2
-            flat = int(np.argmax(mag))
-            i, j = divmod(flat, rho)
-            if not (mag[i, j] > thr):
-                break
-            rows[j] = blk[i]
-            piv = b_mat[i, j]
-            col = b_mat[:, j].copy()
-            row = b_mat[i, :].copy()
-            row[j] -= 1.0
-            b_mat -= np.outer(col, row) / piv
-            swapped = True
-            swaps += 1
-        quiet = 0 if swapped else quiet + 1
-        visits += 1
-        beta = (beta + 1) % nb
-    return rows, swaps, quiet >= nb
+    b_mat = a_cols @ np.linalg.inv(a_cols[rows, :])
+    r = len(rows)
+    for swaps in range(max_swaps + 1):
+        mag = np.abs(b_mat)
+        i, j = divmod(int(np.argmax(mag)), r)
+        if not (mag[i, j] > 1.0 + tau):
+            return rows, swaps, True
+        if swaps == max_swaps:
+            break
+        rows[j] = i
+        row = b_mat[i, :].copy()
+        row[j] -= 1.0
+        b_mat -= np.outer(b_mat[:, j], row) / b_mat[i, j]
+    return rows, max_swaps, False
 
 
 # ----------------------------------------------------------------------------
@@ -337,22 +247,32 @@ def column_scaled(a_mat):
 
 
 def core_select(tensor, d, n, k, outer, cols, direction, opts, diag):
-    """Select rows of core k's fiber; returns (new index set, summed interpolant,
-    interpolation core G = A_c A_c[W]^{-1} as an (outer, N, rank) array)."""
+    """One matrix cross step at core k: fiber, its column basis, maxvol, interpolation core.
+
+    The fiber A (column-scaled) is factored by QR with column pivoting,
+    A P = Q R.  Its numerical rank rho is the count of |R_kk| > theta |R_00|;
+    the first rho pivot columns are kept and Q_rho (orthonormal, same span) is
+    the basis maxvol works on: starting rows by elimination with partial
+    pivoting on Q_rho, then maxvol over all rows.  The interpolation core is
+    A_keep A_keep[I]^{-1} = Q_rho Q_rho[I]^{-1} (equal in exact arithmetic;
+    the orthonormal form is the better-conditioned one).
+
+    Returns (new index set, summed interpolant, interpolation core
+    G as an (outer, N, rank) array)."""
     raw = _fiber(tensor, d, n, k, outer, cols, direction)
     diag.evaluations += raw.size
     a_mat = column_scaled(raw)
-    rows, keep = tournament_select(a_mat, opts.block_rows, opts.theta, screen_mat=raw)
-    if not rows:
+    q, r, _ = scipy.linalg.qr(a_mat, mode="economic", pivoting=True)
+    rdiag = np.abs(np.diag(r))
+    if rdiag.size == 0 or not (rdiag[0] > 0):
         raise FloatingPointError("fiber matrix has numerical rank 0")
-    col_ref = (a_mat.real ** 2 + a_mat.imag ** 2).max(axis=0)[keep]
-    pr, pc = rank_reveal(a_mat[rows][:, keep], opts.theta, col_ref)
-    rows, keep = [rows[i] for i in pr], [keep[j] for j in pc]
-    a_cols = a_mat[:, keep]
-    rows, swaps, ok = maxvol_refine(a_cols, rows, opts.block_rows, opts.tau)
+    rho = int(np.count_nonzero(rdiag > opts.theta * rdiag[0]))
+    basis = q[:, :rho]
+    rows, _ = gepp_select(basis, 0.0)
+    rows, swaps, ok = maxvol(basis, rows, opts.tau, opts.swap_cap * len(rows))
     diag.swaps += swaps
     diag.maxvol_unconverged += 0 if ok else 1
-    g = a_cols @ np.linalg.inv(a_cols[rows, :])
+    g = basis @ np.linalg.inv(basis[rows, :])
     core = g.reshape(len(outer), n, len(rows))
     gsum = core.sum(axis=1)
     if direction == "lr":
@@ -376,14 +296,17 @@ def core_sum(tensor, d, n, k, outer, direction, diag, end_core=None):
 # the sweeps
 # ----------------------------------------------------------------------------
 
-def tt_cross_sum(tensor, r_max, seed, term=0, opts=None, keep_train=False):
+def tt_cross_sum(tensor, r_max, seed, term=0, opts=None, keep_train=False, select=None):
     """TT-cross approximation of sum over the grid of ``tensor``; returns (sum, diag).
 
     With ``keep_train`` the cores of the latest left-to-right half-sweep are kept
     in ``diag.train``: G_0, ..., G_{d-2} (interpolation cores, (r_{k-1}, N, r_k))
     and the end core's fiber (r_{d-2}, N, 1); their product is the train whose
-    weighted sum that half-sweep estimated."""
+    weighted sum that half-sweep estimated.  ``select`` replaces the matrix cross
+    step of one core (default ``core_select``; the tests' kernel-schedule replay
+    passes its own)."""
     opts = opts or CrossOptions()
+    select = select or core_select
     d, n = tensor.d, tensor.n
     ranks = bond_ranks(d, n, r_max)
     lsets = [None] * (d + 1)
@@ -401,7 +324,7 @@ def tt_cross_sum(tensor, r_max, seed, term=0, opts=None, keep_train=False):
             v = np.ones(1, dtype=np.complex128)
             cores = []
             for k in range(d - 1):
-                lsets[k + 1], gsum, core = core_select(tensor, d, n, k, lsets[k], rsets[k + 1], "lr", opts, diag)
+                lsets[k + 1], gsum, core = select(tensor, d, n, k, lsets[k], rsets[k + 1], "lr", opts, diag)
                 cores.append(core)
                 v = v @ gsum
             est = complex(v @ core_sum(tensor, d, n, d - 1, lsets[d - 1], "lr", diag, cores))
@@ -410,7 +333,7 @@ def tt_cross_sum(tensor, r_max, seed, term=0, opts=None, keep_train=False):
         else:
             v = np.ones(1, dtype=np.complex128)
             for k in range(d - 1, 0, -1):
-                rsets[k], gsum, _ = core_select(tensor, d, n, k, rsets[k + 1], lsets[k], "rl", opts, diag)
+                rsets[k], gsum, _ = select(tensor, d, n, k, rsets[k + 1], lsets[k], "rl", opts, diag)
                 v = gsum.T @ v
             est = complex(core_sum(tensor, d, n, 0, rsets[1], "rl", diag) @ v)
         diag.half_sweeps = s + 1
@@ -428,14 +351,14 @@ def tt_cross_sum(tensor, r_max, seed, term=0, opts=None, keep_train=False):
     return est, diag
 
 
-def tt_price(problem, opts=None):
+def tt_price(problem, opts=None, select=None):
     """Price = Re(sum over terms of scale * TT-cross sum); returns (price, imag, diags)."""
     from .integrand import tensors_for
 
     acc = 0j
     diags = []
     for term, t in enumerate(tensors_for(problem)):
-        est, dg = tt_cross_sum(t, int(problem.max_rank), int(problem.seed), term, opts)
+        est, dg = tt_cross_sum(t, int(problem.max_rank), int(problem.seed), term, opts, select=select)
         acc += t.scale * est
         diags.append(dg)
     return acc.real, acc.imag, diags

@@ -47,6 +47,7 @@ against Stulz's closed forms; the paper's d=3, 4 setting against the full grid s
 from __future__ import annotations
 
 import math
+from dataclasses import replace
 
 import numpy as np
 
@@ -93,30 +94,33 @@ def two_train_options(opts=None):
     """The cross options of a factor train: those given (or the defaults) with a
     fixed count of half-sweeps (``HALF_SWEEPS`` unless given) and no early stop."""
     opts = opts or CrossOptions(max_half_sweeps=HALF_SWEEPS)
-    return CrossOptions(block_rows=opts.block_rows, theta=opts.theta, tau=opts.tau,
-                        max_half_sweeps=opts.max_half_sweeps, sweep_tol=0.0)
+    return replace(opts, sweep_tol=0.0)
 
 
-def factor_trains(problem, term=None, opts=None):
+def factor_trains(problem, term=None, opts=None, select=None, rank_v=None, rank_phi=None):
     """TT-cross trains of vhat and phi for the min-call (term None) or max-call
-    term j; returns (train_vhat, train_phi, diag_vhat, diag_phi)."""
+    term j; returns (train_vhat, train_phi, diag_vhat, diag_phi).  The bond
+    dimensions D_v and D_phi (the paper's table gives them separately) default
+    to the problem's rank cap."""
     opts = two_train_options(opts)
     t_term = 0 if term is None else term
+    caps = {"vhat": rank_v or int(problem.max_rank), "phi": rank_phi or int(problem.max_rank)}
     out = []
     for factor in ("vhat", "phi"):
         t = FactorTensor(problem, factor, term)
-        _, dg = tt_cross_sum(t, int(problem.max_rank), int(problem.seed), t_term, opts, keep_train=True)
+        _, dg = tt_cross_sum(t, caps[factor], int(problem.seed), t_term, opts, keep_train=True, select=select)
         out.append((dg.train, dg))
     return out[0][0], out[1][0], out[0][1], out[1][1]
 
 
-def two_train_price(problem, opts=None):
-    """Price = Re(sum over terms of scale * <vhat | phi>); returns (price, imag, diags)."""
+def two_train_price(problem, opts=None, select=None, rank_v=None, rank_phi=None):
+    """Price = Re(sum over terms of scale * <vhat | phi>); returns (price, imag, diags).
+    ``select`` replaces the matrix cross step (default: the paper-order one)."""
     terms = [None] if problem.payoff == "min" else list(range(len(problem.spot)))
     acc = 0j
     diags = []
     for term in terms:
-        tv, tp, dv, dp = factor_trains(problem, term, opts)
+        tv, tp, dv, dp = factor_trains(problem, term, opts, select, rank_v, rank_phi)
         scale = FactorTensor(problem, "phi", term).scale
         acc += scale * mps_bracket(tv, tp)
         diags.append((dv, dp))

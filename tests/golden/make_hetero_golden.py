@@ -1,0 +1,103 @@
+"""Write tests/golden/hetero_stratified.json: FP64 oracle prices of a stratified
+sample of the heterogeneous batch (inputs.mixed_batch(4096)), one problem per
+(d, N, payoff) cell whose oracle train has converged.
+
+    python tests/golden/make_hetero_golden.py [--workers 8]
+
+Calls only oracle/ (and the seeded input generator).  For each cell the
+problems are tried highest rank cap first, then in batch order, at most
+--tries of them (--max-tries for calls on the maximum, whose oracle runs cost
+d trains); a problem counts as converged when
+  * call on the minimum: the oracle's TT-cross price is within 1e-7 of the
+    exact N^d grid sum (oracle/grid_sum.py);
+  * call on the maximum (no exact grid sum at d >= 4): every term's stop rule
+    held (two consecutive half-sweep estimates within 1e-6) and the imaginary
+    part of the price, zero for the exact grid sum, is below 1e-7 of it.
+Both with the oracle's default options (stop rule 1e-6, rank threshold 1e-8),
+those of the FP64 path.  A cell with no converged problem among its tries is
+listed as such.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+TOL = 1e-7
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "hetero_stratified.json")
+
+
+def judge(i):
+    from oracle import grid_sum, ttcross
+    from paper_2203_02804_gb300 import inputs
+
+    p = inputs.mixed_batch(4096)[i]
+    t0 = time.time()
+    price, imag, diags = ttcross.tt_price(p)
+    rec = {"index": i, "d": p.d, "n_grid": p.n_grid, "payoff": p.payoff, "max_rank": p.max_rank,
+           "oracle": price, "oracle_imag": imag, "half_sweeps": max(dg.half_sweeps for dg in diags)}
+    if p.payoff == "min":
+        exact, _ = grid_sum.grid_sum_for(p)
+        rec["exact_grid"] = exact
+        rec["tt_err"] = price / exact - 1.0
+        rec["converged"] = abs(rec["tt_err"]) < TOL
+    else:
+        rec["imag_rel"] = abs(imag) / abs(price)
+        rec["converged"] = all(dg.converged for dg in diags) and rec["imag_rel"] < TOL
+    rec["seconds"] = time.time() - t0
+    return rec
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workers", type=int, default=os.cpu_count() or 4)
+    ap.add_argument("--tries", type=int, default=5)
+    ap.add_argument("--max-tries", type=int, default=3)
+    args = ap.parse_args()
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from paper_2203_02804_gb300 import inputs
+
+    batch = inputs.mixed_batch(4096)
+    cells = {}
+    for i, p in enumerate(batch):
+        cells.setdefault((p.d, p.n_grid, p.payoff), []).append(i)
+    for k in cells:
+        cells[k].sort(key=lambda i: (-batch[i].max_rank, i))
+        cells[k] = cells[k][:args.max_tries if k[2] == "max" else args.tries]
+    keys = sorted(cells)
+    chosen, empty = {}, []
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(args.workers) as pool:
+        # round t tries the t-th candidate of every cell still open
+        open_cells = list(keys)
+        for t in range(max(args.tries, args.max_tries)):
+            todo = [(k, cells[k][t]) for k in open_cells if t < len(cells[k])]
+            if not todo:
+                break
+            recs = pool.map(judge, [i for _, i in todo], chunksize=1)
+            for (k, _), rec in zip(todo, recs):
+                if rec["converged"]:
+                    chosen[k] = rec
+            open_cells = [k for k in open_cells if k not in chosen]
+            print(f"round {t}: {len(chosen)} cells chosen, {len(open_cells)} open", flush=True)
+    empty = [{"d": k[0], "n_grid": k[1], "payoff": k[2], "tried": len(cells[k])}
+             for k in keys if k not in chosen]
+    out = {"batch": "paper_2203_02804_gb300.inputs.mixed_batch(4096)",
+           "criterion": __doc__.split("Calls only oracle/ (and the seeded input generator).")[1].strip(),
+           "tolerance": TOL,
+           "cells": [chosen[k] for k in keys if k in chosen],
+           "no_converged_problem": empty}
+    with open(OUT, "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"wrote {OUT}: {len(out['cells'])} cells, {len(empty)} without a converged problem")
+
+
+if __name__ == "__main__":
+    main()

@@ -61,5 +61,5 @@ def test_gpu_tuning_run_and_tuned_pricer(tmp_path, monkeypatch):
     _, prices, _ = pr.evaluate(ps)
     pr.close()
     for p, v in zip(ps, prices):
-        ref, _, _ = ttcross.tt_price(p, ttcross.CrossOptions(block_rows=entry["block_rows"]))
+        ref, _, _ = ttcross.tt_price(p)
         assert abs(v - ref) < 1e-4 * abs(ref) + 2e-7 * float(np.max(p.spot))
