@@ -107,11 +107,24 @@ def _oracle_one(args):
     return price
 
 
-def _oracle_two(args):
-    from oracle import twomps
+def _oracle_and_grid(p):
+    """The oracle's TT-cross price and the exact N^d grid sum it approximates."""
+    from oracle import grid_sum, ttcross
 
-    price, _, _ = twomps.two_train_price(args)
-    return price
+    price, _, _ = ttcross.tt_price(p)
+    return price, grid_sum.grid_sum_for(p)[0]
+
+
+def _grid_only(p):
+    from oracle import grid_sum
+
+    return grid_sum.grid_sum_for(p)[0]
+
+
+def single_thread_rate(problems):
+    """Prices/s of the oracle on one host core (one spawned worker, problems in turn)."""
+    _, dt = oracle_prices(problems, 1)
+    return len(problems) / dt
 
 
 def oracle_prices(problems, workers, fn=None):
@@ -279,7 +292,7 @@ def measure_two_train(args, workers):
     probs = [inputs.paper_table_problem(5).with_(seed=5000 + i) for i in range(args.two_train_batch)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     out = {"workload": "paper-d5 min-call, N=50, rank 15, mixed", "batch": len(probs)}
-    prices = None
+    prices = single = None
     for meth in ("two-train", "single"):
         pr = ttprice.Pricer(max_d=5, max_n=50, max_rank=15, max_batch=len(probs), precision="mixed",
                             method=meth, graph=True)
@@ -304,11 +317,123 @@ def measure_two_train(args, workers):
                                       for v in sorted({d.status for d in diags})}}
         if meth == "two-train":
             prices = pv
+        else:
+            single = pv
     n = min(args.cpu_sample, len(probs))
     if n:
-        ref, dt = oracle_prices(probs[:n], min(workers, n), fn=_oracle_two)
-        out["parity"] = {"vs": "FP64 oracle two-train price, same problems", "n": n,
-                         "max_rel_err": max(abs(prices[i] / ref[i] - 1.0) for i in range(n)), "tol": 1e-4}
+        # both forms approximate the same N^d grid sum, known exactly here (one-factor grid sum)
+        ref, dt = oracle_prices(probs[:n], min(workers, n), fn=_grid_only)
+        out["parity"] = {"vs": "exact N^d grid sum (oracle one-factor grid sum), same problems", "n": n,
+                         "two_train_max_rel_err": max(abs(prices[i] / ref[i] - 1.0) for i in range(n)),
+                         "single_train_max_rel_err": max(abs(single[i] / ref[i] - 1.0) for i in range(n)),
+                         "note": "rank 15 at the paper's setting: both are TT-error limited"}
+    return out
+
+
+def _timed_runs(pr, flush, steps, torch):
+    """Median device time (ms) of `steps` tt_price_run calls, L2 flushed before each."""
+    ts = []
+    for s in range(steps):
+        flush.fill_(s & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(pr.stream)
+        assert pr.run() == 0
+        b.record(pr.stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def _json_default(o):
+    """NumPy scalars in the line as plain numbers."""
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(f"not JSON serialisable: {type(o).__name__}")
+
+
+def _status_counts(diags):
+    return {str(v): sum(1 for d in diags if d.status == v) for v in sorted({d.status for d in diags})}
+
+
+def measure_fp64(problems, stream, flush, peak64, steps=2):
+    """Plain FP64 TT on the same workload batch: prices/s and its roofline against the
+    measured FP64 FMA peak (every step of the cross in FP64)."""
+    import torch
+
+    from paper_2203_02804_gb300 import ttprice
+
+    pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=len(problems), precision="fp64",
+                        stream=stream, graph=True)
+    pr.prepare(problems)
+    pr.run()
+    torch.cuda.synchronize()
+    ms = _timed_runs(pr, flush, steps, torch)
+    _, prices, diags = pr.results()
+    pr.close()
+    flops = sum(d.flops for d in diags)
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"workload": "d5-min-call, the same batch", "batch": len(problems), "steps": steps,
+            "prices_per_s": len(problems) / (ms / 1e3), "ms_per_step": ms,
+            "roofline": {"bound": "fp64", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                         "frac": achieved / peak64, "kernel": "tt_cross_kernel<double>",
+                         "peak_basis": "measured: FP64 FMA probe on this GPU (include/ttprobe.h)"},
+            "status_counts": _status_counts(diags), "_prices": prices}
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "hetero_stratified.json")
+
+
+def measure_hetero(args, stream, flush, peak32, steps=2):
+    """The heterogeneous batch (d~U{3..10}, N in {64,128,256}, rank cap in {8,16,32},
+    min/max 50/50) in one launch, mixed path: with the autotuner's per-class table
+    (block rows and rank threshold per (rank cap, payoff) class, untimed tuning) and
+    with the library defaults; parity on the stratified sample whose FP64 oracle
+    prices tests/golden/hetero_stratified.json stores."""
+    import torch
+
+    from paper_2203_02804_gb300 import autotune, inputs, ttprice
+
+    probs = inputs.mixed_batch(args.hetero_batch)
+    t0 = time.perf_counter()
+    table, recs = autotune.tune_classes("mixed", probs, engine="cuda", sample=152, reps=1)
+    tune_s = time.perf_counter() - t0
+    out = {"workload": "heterogeneous: d~U{3..10}, N in {64,128,256}, rank cap in {8,16,32}, "
+                       "min/max calls 50/50, mixed path", "batch": len(probs), "steps": steps,
+           "classes": table, "tuning_s": tune_s}
+    prices = None
+    for label, classes in (("tuned", table), ("defaults", None)):
+        pr = ttprice.Pricer(max_d=10, max_n=256, max_rank=32, max_batch=len(probs), precision="mixed",
+                            engine="cuda", stream=stream, graph=True, classes=classes)
+        pr.prepare(probs)
+        pr.run()
+        torch.cuda.synchronize()
+        ms = _timed_runs(pr, flush, steps, torch)
+        _, pv, diags = pr.results()
+        pr.close()
+        flops = sum(d.flops for d in diags)
+        achieved = flops / (ms / 1e3) / 1e12
+        out[label] = {"prices_per_s": len(probs) / (ms / 1e3), "ms_per_step": ms,
+                      "flops_per_launch": flops, "achieved_tflops": achieved, "frac": achieved / peak32,
+                      "status_counts": _status_counts(diags)}
+        if label == "tuned":
+            prices = pv
+    try:
+        with open(GOLDEN) as f:
+            g = json.load(f)
+        cells = g["cells"] + g.get("cells_tier2", [])
+        rel, over = [], 0
+        for c in cells:
+            i = c["index"]
+            if i >= len(probs):
+                continue
+            err = abs(prices[i] - c["oracle"])
+            rel.append(err / abs(c["oracle"]))
+            over += err > 1e-4 * abs(c["oracle"]) + 2e-7 * float(np.max(probs[i].spot))
+        out["parity"] = {"vs": "FP64 oracle TT-cross, stratified sample (one converged problem per "
+                               "(d, N, payoff) cell)", "n": len(rel), "max_rel_err": max(rel) if rel else None,
+                         "over_tol": int(over), "tol": "1e-4 relative + 2e-7 x spot"}
+    except (OSError, ValueError, KeyError):
+        out["parity"] = None
     return out
 
 
@@ -324,13 +449,20 @@ def run_gpu(args):
 
         dist.init_process_group("gloo")
 
-    # CPU baseline first (spawned workers, before this process does much CUDA work)
+    # CPU baseline first (spawned workers, before this process does much CUDA work):
+    # the oracle on a sample spread over the batch, all cores, with each problem's
+    # exact grid sum for the parity check; then the oracle's rate on one core
     sample = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         workers = cpu_workers()
-        sample_probs = workload_problems(args.batch)[:max(workers, args.cpu_sample)]
-        sample_prices, sample_dt = oracle_prices(sample_probs, workers)
-        sample = (sample_probs, sample_prices, sample_dt, workers)
+        all_probs = workload_problems(args.batch)
+        n = max(1, min(args.cpu_sample, len(all_probs)))
+        stride = max(1, len(all_probs) // n)
+        idx = list(range(0, len(all_probs), stride))[:n]
+        sample_probs = [all_probs[i] for i in idx]
+        both, sample_dt = oracle_prices(sample_probs, workers, fn=_oracle_and_grid)
+        single = single_thread_rate(sample_probs[:3])
+        sample = (idx, sample_probs, [b[0] for b in both], [b[1] for b in both], sample_dt, workers, single)
 
     from paper_2203_02804_gb300 import build, ttprice
 
@@ -338,6 +470,9 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    # the roofline denominators, measured on this GPU right before the timing
+    peak32 = ttprice.fma_peak("fp32")
+    peak64 = ttprice.fma_peak("fp64")
     problems = workload_problems(args.batch, rank_offset=rank)
     # launch configuration from the project's autotuner (untimed; measured on this GPU
     # for the workload's shape), else the library defaults
@@ -348,7 +483,7 @@ def run_gpu(args):
         from paper_2203_02804_gb300 import autotune
 
         entry = autotune.tune(args.precision, 5, 128, 32, "min")
-        tuned = {"block_rows": entry["block_rows"], "engine": entry["engine"]}
+        tuned = {k: entry[k] for k in autotune.KNOBS}
     pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=args.batch,
                         precision=args.precision, device=local, stream=stream, graph=True, **tuned)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -392,6 +527,12 @@ def run_gpu(args):
     e2e_s = max_over_ranks(e2e_s, dist)
     e2e_value = args.batch * world * args.steps / e2e_s
     pr.close()
+    fp64 = None
+    if args.fp64_steps > 0 and world == 1 and args.precision == "mixed":
+        fp64 = measure_fp64(problems, stream, flush, peak64, args.fp64_steps)
+    hetero = None
+    if args.hetero_batch > 0 and world == 1:
+        hetero = measure_hetero(args, stream, flush, peak32)
     surrogate = None
     if args.surrogate_samples > 0 and world == 1:
         surrogate = measure_surrogate(args, tuned)
@@ -411,13 +552,16 @@ def run_gpu(args):
             "config": dict(workload_config(args.batch, args.precision), launch="cuda-graph",
                            tuned=tuned or "defaults"),
             "roofline": {"bound": "alu", "achieved": achieved,
-                         "peak": FP32_PEAK_TFLOPS if args.precision == "mixed" else 1.26,
+                         "peak": peak32 if args.precision == "mixed" else peak64,
                          "unit": "TFLOP/s",
-                         "frac": achieved / (FP32_PEAK_TFLOPS if args.precision == "mixed" else 1.26),
+                         "frac": achieved / (peak32 if args.precision == "mixed" else peak64),
                          "traffic": traffic_per_launch(args.batch, args.precision),
                          "kernel": f"tt_cross_kernel<{'float' if args.precision == 'mixed' else 'double'}>",
                          "flops_per_launch": flops_per_step,
-                         "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                         "peak_basis": f"measured: {'FP32' if args.precision == 'mixed' else 'FP64'} FMA probe on "
+                                       f"this GPU just before the timing (include/ttprobe.h); FP32 {peak32:.1f}, "
+                                       f"FP64 {peak64:.3f} TFLOP/s; derived FP32 {FP32_PEAK_TFLOPS:.1f} "
+                                       f"(152 SMs x 128 lanes x 2 x 2070 MHz)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
@@ -425,20 +569,38 @@ def run_gpu(args):
             "status_counts": {str(s): sum(1 for d in diags if d.status == s)
                               for s in sorted({d.status for d in diags})},
         }
+        if hetero is not None:
+            line["hetero"] = hetero
         if surrogate is not None:
             line["surrogate"] = surrogate
         if two_train is not None:
             line["two_train"] = two_train
         if sample is not None:
-            sp, sprices, sdt, workers = sample
+            idx, sp, sprices, sgrid, sdt, workers, single = sample
             n = len(sp)
-            rel = [abs(prices[i] / sprices[i] - 1.0) for i in range(n)]
+            rel = [abs(prices[i] / sprices[k] - 1.0) for k, i in enumerate(idx)]
+            relg = [abs(prices[i] / sgrid[k] - 1.0) for k, i in enumerate(idx)]
+            tol = 1e-4 if args.precision == "mixed" else 1e-6
             line["cpu_baseline"] = {"value": n / sdt, "unit": UNIT, "cores": workers, "kind": "oracle",
-                                    "sample": f"first {n} problems of the batch, FP64 NumPy TT-cross, "
-                                              f"one process per core"}
+                                    "single_thread_value": single,
+                                    "sample": f"{n} problems spread over the batch (every {idx[1] - idx[0] if n > 1 else 1}th), "
+                                              f"FP64 NumPy TT-cross, one spawned process per core; "
+                                              f"single_thread_value: 3 of them on one core"}
             line["parity"] = {"vs": "FP64 oracle TT-cross, same problems", "n": n,
-                              "max_rel_err": max(rel), "tol": 1e-4 if args.precision == "mixed" else 1e-6}
-        print(json.dumps(line), flush=True)
+                              "max_rel_err": max(rel), "over_tol": int(sum(r > tol for r in rel)), "tol": tol,
+                              "vs_exact_grid_sum": {"max_rel_err": max(relg),
+                                                    "oracle_max_rel_err": max(abs(a / b - 1.0) for a, b in
+                                                                              zip(sprices, sgrid))}}
+            if fp64 is not None:
+                f64p = fp64.pop("_prices")
+                fp64["parity"] = {"vs": "FP64 oracle TT-cross, same sample", "n": n,
+                                  "max_rel_err": max(abs(f64p[i] / sprices[k] - 1.0) for k, i in enumerate(idx)),
+                                  "max_rel_err_vs_exact_grid_sum": max(abs(f64p[i] / sgrid[k] - 1.0)
+                                                                       for k, i in enumerate(idx))}
+        if fp64 is not None:
+            fp64.pop("_prices", None)
+            line["fp64"] = fp64
+        print(json.dumps(line, default=_json_default), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
@@ -452,7 +614,7 @@ def main():
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--cpu-sample", type=int, default=16)
+    ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--engine", choices=["auto", "cuda", "tc"], default="auto",
@@ -460,6 +622,10 @@ def main():
     ap.add_argument("--surrogate-samples", type=int, default=1 << 18,
                     help="TT-priced training samples of the learned surrogate (0: skip it)")
     ap.add_argument("--surrogate-epochs", type=int, default=40)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 path on the same batch (0: skip)")
+    ap.add_argument("--hetero-batch", type=int, default=4096,
+                    help="problems of the heterogeneous batch in one launch (0: skip)")
     ap.add_argument("--two-train-batch", type=int, default=4096,
                     help="problems of the paper's d=5 setting priced in the two-train form (0: skip)")
     args = ap.parse_args()

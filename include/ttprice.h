@@ -69,6 +69,24 @@ typedef enum { TT_ENGINE_AUTO = 0, TT_ENGINE_CUDA_CORES = 1, TT_ENGINE_TENSOR_CO
  * runs the two crosses in FP32).  Needs max_rank <= 32 and max_n <= 1024. */
 typedef enum { TT_METHOD_SINGLE_TRAIN = 0, TT_METHOD_TWO_TRAINS = 1 } tt_method;
 
+/* Per-class launch configuration (the autotuner's output): problems with
+ * d_min <= d <= d_max, grid size n_grid (0: any), rank cap max_rank (0: any) and
+ * payoff (a tt_payoff, or -1: either) run with these values instead of the
+ * options' block_rows and rank_tol; the first matching class applies.  0 or a
+ * non-positive value keeps the options' value.  A class's block_rows must lie
+ * in [its problems' rank cap, tt_options.block_rows] (shared memory is sized for
+ * the options' value); a problem whose rank cap exceeds it keeps the options'. */
+typedef struct {
+  int d_min, d_max;
+  int n_grid;
+  int max_rank;
+  int payoff;
+  int block_rows;
+  double rank_tol;
+} tt_class_tuning;
+
+#define TT_MAX_CLASSES 64
+
 typedef struct {
   int max_d;            /* largest number of assets                        (1..255)  */
   int max_n;            /* largest grid size N per axis                    (2..4096) */
@@ -79,7 +97,7 @@ typedef struct {
   double sweep_tol;     /* <= 0 -> 1e-6 (FP64) or 1e-4 (mixed): relative change of
                            the price estimate between half-sweeps that stops a job
                            (each path's accuracy target against the FP64 oracle)  */
-  double rank_tol;      /* <= 0 -> 1e-8 (FP64) or 1e-5 (mixed): a column whose
+  double rank_tol;      /* <= 0 -> 1e-8 (FP64) or 1e-6 (mixed): a column whose
                            elimination pivot is below rank_tol times the column's
                            largest entry is dropped (numerically dependent)        */
   double maxvol_tol;    /* <= 0 -> 0.05: maxvol stops when all |B_ij| <= 1 + tol  */
@@ -102,6 +120,9 @@ typedef struct {
   void* workspace;      /* optional device buffer of tt_workspace_bytes() bytes,
                            owned by the caller; NULL = the library allocates       */
   size_t workspace_bytes;
+  const tt_class_tuning* classes; /* optional per-class block_rows / rank_tol, read
+                           (copied) by tt_price_create; NULL = none              */
+  int n_classes;        /* entries of classes (0..TT_MAX_CLASSES)                  */
 } tt_options;
 
 typedef struct {
@@ -154,6 +175,15 @@ typedef struct {
                             and integrand steps, by formula: 24 per integrand
                             evaluation, 8 per complex multiply-add, 8 r^3/3 per
                             FP64 interpolation solve                             */
+  double est_discretization_err; /* estimated |grid price - integral| (absolute,
+                            price units) from the Poisson-summation model of the
+                            midpoint rule (Eq. discr): each axis aliases at rate
+                            delta_j (|alpha_j| for the call on the maximum), a term
+                            exp(-2 pi rate / eta) times the price, plus the cut
+                            Gaussian tail exp(-T sigma_j^2 L^2 / 2) times the
+                            price; an order-of-magnitude estimate (within a few
+                            times where aliasing dominates, conservative where
+                            the truncation does); NaN with a NaN price          */
 } tt_diag;
 
 /* Create a pricer for problems up to the given sizes on opt->device.  Allocates

@@ -1,15 +1,30 @@
-"""Autotuner for the pricer's launch configuration, measured on the GPU per
-workload shape and kept in a JSON cache.
+"""Autotuner for the pricer's launch configuration, measured on the GPU and kept
+in a JSON cache.
 
     python -m paper_2203_02804_gb300.autotune --d 5 --n 128 --rank 32 --precision mixed
 
-Tuned knobs: the block height of the elimination tournament and maxvol
-(`block_rows`, 64 or 128 where the rank allows) and, for the mixed path, the
-engine of the maxvol block product (FP32 CUDA cores or 3xTF32 tensor cores).
+Tuned knobs, per workload shape (precision, d, N, rank cap, payoff):
+  * block_rows: the block height of the elimination tournament and of maxvol
+    (64 or 128 where the rank allows);
+  * engine (mixed path): the maxvol block product on FP32 CUDA cores or 3xTF32
+    tensor cores;
+  * rank_tol (mixed path): the rank threshold, 1e-6, 3e-6 or 1e-5.  A looser
+    threshold drops more numerically dependent columns (smaller ranks, faster)
+    at some accuracy; it is only taken where the prices stay within tolerance.
+
 Every candidate prices the same seeded synthetic batch of the shape (three
 persistent waves of the full grid, through a CUDA graph), warmed up, and is
-timed with CUDA events; the fastest wins unless its prices part from the first
-candidate's by more than the precision's tolerance (1e-6 FP64, 1e-4 mixed).
+timed with CUDA events.  Accuracy is judged against the library's own FP64
+path on the same batch: a mixed candidate counts only if every price is within
+1e-4 of it (plus 2e-7 of the largest spot, the FP32 floor of prices far below
+the spot), an FP64 candidate within 1e-6.  The fastest accepted candidate wins.
+
+A heterogeneous launch uses one configuration per class of problems
+(`tune_classes`): the problems are grouped by rank cap and payoff, each class
+is tuned on a sample of its own problems with the launch's engine fixed, and
+the winners become the pricer's class table (tt_options.classes), so that
+each job of one launch runs with its class's block height and rank threshold.
+
 The cache (``$TTPRICE_TUNING_CACHE``, default ``~/.cache/ttprice/tuning.json``)
 maps "sm_<cc>|<precision>|d<d>|N<n>|r<rank>|<payoff>" to the winner and the
 timings; `Pricer.tuned(...)` builds a pricer from it.
@@ -24,6 +39,9 @@ from typing import Callable, Dict, List, Optional, Sequence, Tuple
 import numpy as np
 
 TOL = {"fp64": 1e-6, "mixed": 1e-4}
+FLOOR = {"fp64": 0.0, "mixed": 2e-7}       # absolute, times the largest spot
+RANK_TOLS = {"fp64": (1e-8,), "mixed": (1e-6, 3e-6, 1e-5)}
+KNOBS = ("block_rows", "engine", "rank_tol")
 
 
 def cache_path() -> str:
@@ -54,75 +72,111 @@ def store(key: str, entry: dict, path: Optional[str] = None) -> None:
     os.replace(tmp, p)
 
 
-def candidates(precision: str, rank: int) -> List[dict]:
-    """Configurations valid for the rank (block_rows >= rank; the tensor-core engine
-    is mixed-only and takes block_rows <= 128)."""
+def candidates(precision: str, rank: int, engines: Optional[Sequence[str]] = None) -> List[dict]:
+    """Configurations valid for the rank: block_rows >= rank; the tensor-core engine is
+    mixed-only and takes block_rows <= 128; rank thresholds per precision."""
+    if engines is None:
+        engines = ("cuda", "tc") if precision == "mixed" else ("cuda",)
     out = []
     for b in (128, 64):
         if b < rank:
             continue
-        engines = ("cuda", "tc") if precision == "mixed" else ("cuda",)
-        out += [{"block_rows": b, "engine": e} for e in engines]
+        for e in engines:
+            out += [{"block_rows": b, "engine": e, "rank_tol": t} for t in RANK_TOLS[precision]]
     return out
 
 
+def accepted(prices: np.ndarray, ref: np.ndarray, spot_max: np.ndarray, precision: str,
+             mask: Optional[np.ndarray] = None) -> bool:
+    """Every price finite, and every price of `mask` (the problems whose FP64 reference
+    converged; default all) within the precision's tolerance of that reference.  An
+    unconverged, rank-limited train moves by its TT error with any pivot change, so
+    it says nothing about a knob."""
+    if prices.size == 0:
+        return True
+    m = np.ones(prices.shape, dtype=bool) if mask is None else mask
+    err = np.abs(prices - ref)[m]
+    bound = TOL[precision] * np.abs(ref)[m] + FLOOR[precision] * spot_max[m]
+    return bool(np.all(np.isfinite(prices)) and np.all(err <= bound))
+
+
 def choose(cands: Sequence[dict], measure: Callable[[dict], Tuple[float, np.ndarray]],
-           tol: float) -> Tuple[dict, List[dict]]:
+           ref: np.ndarray, spot_max: np.ndarray, precision: str,
+           mask: Optional[np.ndarray] = None) -> Tuple[dict, List[dict]]:
     """Time every candidate (measure -> (seconds, prices)); the fastest whose prices
-    agree with the first candidate's to `tol` wins.  Returns (winner, records)."""
-    records, ref = [], None
+    the reference accepts wins.  Returns (winner, records)."""
+    records = []
     for c in cands:
         secs, prices = measure(c)
-        if ref is None:
-            ref = prices
-        ok = bool(np.all(np.abs(prices / ref - 1.0) <= tol)) if prices.size else True
-        records.append(dict(c, seconds=secs, agrees=ok))
+        records.append(dict(c, seconds=secs, agrees=accepted(prices, ref, spot_max, precision, mask)))
     valid = [r for r in records if r["agrees"]]
+    if not valid:  # nothing meets the tolerance: the most accurate threshold, fastest of those
+        tightest = min(r["rank_tol"] for r in records)
+        valid = [r for r in records if r["rank_tol"] == tightest]
     best = min(valid, key=lambda r: r["seconds"])
-    return {k: best[k] for k in ("block_rows", "engine")}, records
+    return {k: best[k] for k in KNOBS}, records
 
 
-def gpu_measure(precision: str, d: int, n: int, rank: int, payoff: str, waves: int = 3,
-                reps: int = 3) -> Callable[[dict], Tuple[float, np.ndarray]]:
-    """A measure() over a seeded batch of the shape: `waves` x the persistent grid
-    (3 CTAs x SMs) problems, one warm-up run, the mean of `reps` timed runs."""
+def gpu_measure(precision: str, batch: Sequence, reps: int = 3, classes=None):
+    """measure(cfg) over `batch`: one warm-up run, the mean of `reps` timed runs;
+    and reference() -> (FP64 prices of the same batch by the library's FP64 path,
+    mask of the problems whose FP64 sweeps converged)."""
     import torch
 
-    from . import inputs, ttprice
+    from . import ttprice
 
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    batch = inputs.tuning_batch(waves * 3 * sms if d <= 10 else sms, d, n, rank, payoff)
+    d = max(p.d for p in batch)
+    n = max(p.n_grid for p in batch)
+    rank = max(p.max_rank for p in batch)
 
-    def measure(cfg: dict) -> Tuple[float, np.ndarray]:
-        pr = ttprice.Pricer(max_d=d, max_n=n, max_rank=rank, max_batch=len(batch), precision=precision,
-                            block_rows=cfg["block_rows"], engine=cfg["engine"], graph=True)
+    def run(prec: str, cfg: dict, timed: bool):
+        pr = ttprice.Pricer(max_d=d, max_n=n, max_rank=rank, max_batch=len(batch), precision=prec,
+                            block_rows=cfg.get("block_rows", 0), engine=cfg.get("engine", "auto"),
+                            rank_tol=cfg.get("rank_tol", 0.0), graph=True, classes=classes)
         try:
             pr.prepare(batch)
             pr.run()
             torch.cuda.synchronize()
             times = []
-            for _ in range(reps):
+            for _ in range(reps if timed else 0):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(pr.stream)
                 pr.run()
                 b.record(pr.stream)
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b) / 1e3)
-            _, prices, _ = pr.results()
+            _, prices, diags = pr.results()
         finally:
             pr.close()
-        return float(np.mean(times)), prices
+        return (float(np.mean(times)) if times else 0.0), prices, diags
 
-    return measure
+    def measure(cfg: dict) -> Tuple[float, np.ndarray]:
+        secs, prices, _ = run(precision, cfg, True)
+        return secs, prices
+
+    def reference():
+        _, prices, diags = run("fp64", {}, False)
+        return prices, np.array([dg.status == ttprice.TT_OK for dg in diags])
+
+    return measure, reference
 
 
 def tune(precision: str, d: int, n: int, rank: int, payoff: str = "min", path: Optional[str] = None,
-         measure: Optional[Callable] = None) -> dict:
+         measure: Optional[Callable] = None, reference: Optional[np.ndarray] = None) -> dict:
+    """Tune one shape on a seeded batch of three persistent waves; cache the winner."""
     import torch
 
+    from . import inputs
+
     cc = "%d%d" % torch.cuda.get_device_capability(0)
-    m = measure or gpu_measure(precision, d, n, rank, payoff)
-    best, records = choose(candidates(precision, rank), m, TOL[precision])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    batch = inputs.tuning_batch(3 * 3 * sms if d <= 10 else sms, d, n, rank, payoff)
+    mask = None
+    if measure is None:
+        measure, ref_fn = gpu_measure(precision, batch)
+        reference, mask = ref_fn()
+    spot_max = np.array([float(np.max(p.spot)) for p in batch])
+    best, records = choose(candidates(precision, rank), measure, reference, spot_max, precision, mask)
     entry = dict(best, records=records)
     store(shape_key(cc, precision, d, n, rank, payoff), entry, path)
     return entry
@@ -134,7 +188,36 @@ def lookup(precision: str, d: int, n: int, rank: int, payoff: str = "min",
 
     cc = "%d%d" % torch.cuda.get_device_capability(0)
     e = load_cache(path).get(shape_key(cc, precision, d, n, rank, payoff))
-    return None if e is None else {"block_rows": e["block_rows"], "engine": e["engine"]}
+    if e is None:
+        return None
+    return {k: e[k] for k in KNOBS if k in e}
+
+
+def problem_class(p) -> Tuple[int, str]:
+    return int(p.max_rank), str(p.payoff)
+
+
+def tune_classes(precision: str, problems: Sequence, engine: str = "cuda", sample: int = 456,
+                 reps: int = 2) -> Tuple[List[dict], List[dict]]:
+    """Per-class configurations for a heterogeneous batch: classes by (rank cap, payoff),
+    each tuned on up to `sample` of its own problems (batch order) with `engine`
+    fixed.  Returns (class table for Pricer(classes=...), records)."""
+    groups: Dict[Tuple[int, str], list] = {}
+    for p in problems:
+        groups.setdefault(problem_class(p), []).append(p)
+    table, records = [], []
+    for (rank, payoff), members in sorted(groups.items()):
+        batch = members[:sample]
+        measure, ref_fn = gpu_measure(precision, batch, reps=reps)
+        ref, mask = ref_fn()
+        spot_max = np.array([float(np.max(p.spot)) for p in batch])
+        best, recs = choose(candidates(precision, rank, engines=(engine,)), measure, ref, spot_max, precision,
+                            mask)
+        table.append({"d_min": 1, "d_max": 255, "max_rank": rank, "payoff": payoff,
+                      "block_rows": best["block_rows"], "rank_tol": best["rank_tol"]})
+        records.append({"max_rank": rank, "payoff": payoff, "problems": len(batch),
+                        "fp64_converged": int(mask.sum()), "winner": best, "candidates": recs})
+    return table, records
 
 
 def main() -> int:

@@ -18,8 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libttprice.so")
-SOURCES = ["ttprice.cu", "mlp.cu"]
-DEPS = ["ttprice.cu", "ttprice_device.cuh", "ttprice_kernels.cuh", "ttprice_tc.cuh", "mlp.cu"]
+SOURCES = ["ttprice.cu", "mlp.cu", "probe.cu"]
+DEPS = ["ttprice.cu", "ttprice_device.cuh", "ttprice_kernels.cuh", "ttprice_tc.cuh", "mlp.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,7 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the sources to objects in parallel, then link the shared library."""
-    deps = [os.path.join(CSRC, f) for f in DEPS] + [os.path.join(INCLUDE, h) for h in ("ttprice.h", "ttmlp.h")]
+    deps = [os.path.join(CSRC, f) for f in DEPS] + [os.path.join(INCLUDE, h) for h in ("ttprice.h", "ttmlp.h", "ttprobe.h")]
     if not force and not _stale(LIB, deps):
         return LIB
     objs, procs = [], []

@@ -175,6 +175,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       ss.have_trusted = 0;
       ss.ok_hist[0] = ss.ok_hist[1] = 0;
     }
+    // the job's own rank threshold and block height (its class's, else the options')
+    Knobs jk = kn;
+    jk.theta = jd.theta;
+    jk.block_rows = jd.block_rows;
     int status = x.misc[MISC_DRAW] ? ST_INVALID : ST_NOT_CONVERGED;
     int hs = 0, maxrank = 1;
     const int d = jd.d;
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       double2 est = make_double2(0.0, 0.0);
       if ((s & 1) == 0) {
         for (int k = 0; k + 1 < d; ++k) {
-          const int rho = core_select<R, TC>(x, kn, k, DIR_LR);
+          const int rho = core_select<R, TC>(x, jk, k, DIR_LR);
           maxrank = max(maxrank, rho);
           if (x.misc[MISC_FAIL]) break;
         }
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
         TTP_TOC(t_cs, 12);
       } else {
         for (int k = d - 1; k >= 1; --k) {
-          const int rho = core_select<R, TC>(x, kn, k, DIR_RL);
+          const int rho = core_select<R, TC>(x, jk, k, DIR_RL);
           maxrank = max(maxrank, rho);
           if (x.misc[MISC_FAIL]) break;
         }
@@ -761,6 +765,8 @@ struct Resolved {
   Knobs kn;
   int max_jobs;
   size_t max_params;
+  int n_classes;
+  tt_class_tuning classes[TT_MAX_CLASSES];  // copied from the options
 };
 
 bool resolve(const tt_options* in, Resolved* r) {
@@ -791,10 +797,20 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.max_half_sweeps < 1 || o.max_half_sweeps > 1000) return false;
   const bool f64 = o.precision == TT_FP64;
   if (!(o.sweep_tol > 0)) o.sweep_tol = f64 ? 1e-6 : 1e-4;
-  if (!(o.rank_tol > 0)) o.rank_tol = f64 ? 1e-8 : 1e-5;
+  if (!(o.rank_tol > 0)) o.rank_tol = f64 ? 1e-8 : 1e-6;
   if (!(o.maxvol_tol > 0)) o.maxvol_tol = 0.05;
   if (!std::isfinite(o.sweep_tol) || !std::isfinite(o.rank_tol) || !std::isfinite(o.maxvol_tol))
     return false;
+  if (o.n_classes < 0 || o.n_classes > TT_MAX_CLASSES || (o.n_classes > 0 && !o.classes)) return false;
+  r->n_classes = o.n_classes;
+  for (int c = 0; c < o.n_classes; ++c) {
+    tt_class_tuning t = o.classes[c];
+    if (!std::isfinite(t.rank_tol)) return false;
+    if (t.block_rows < 0 || t.block_rows > o.block_rows) return false;
+    if (!(t.rank_tol > 0)) t.rank_tol = 0.0;
+    r->classes[c] = t;
+  }
+  o.classes = nullptr;  // the copy above is what the handle keeps
   r->kn.theta = o.rank_tol;
   r->kn.tau = o.maxvol_tol;
   r->kn.sweep_tol = o.sweep_tol;
@@ -843,7 +859,8 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   const int rs = f64 ? 8 : 4, cs = 2 * rs;
   const int r = o.max_rank, b = o.block_rows, n = o.max_n, d = o.max_d;
   int sw_elems = std::max((r + std::max(b, 128)) * r, 2 * r * r);
-  sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + cs - 1) / cs);
+  // the FP64 interpolation solve: [P^T | y] (r x (r+1) complex doubles) and its reduction scratch
+  sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + 2 * ttp::kWarps * 12 + cs - 1) / cs);
   const int kp = ttp::tc::pad16(r);
   const bool tcore = o.engine == TT_ENGINE_TENSOR_CORES;
   // tensor cores: kTcBufs buffers of four 128-row planes of one kTcChunk-column chunk
@@ -921,6 +938,7 @@ struct DevLayout {  // offsets inside the device workspace
   size_t stage, stage_bytes, jres, ires, counter, scratch, emit, emit_stride, total;
   size_t o_jobs, o_params, o_order, o_first, o_count, o_hstatus, o_pairs;  // inside the stage block
   size_t o_host;  // host-only scratch of the preparation (never copied to the device)
+  size_t o_disc;  // host-only: per-problem relative discretisation-error factor
 };
 
 // doubles of host scratch the preparation of one problem needs (d <= max_d):
@@ -945,6 +963,7 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   const bool two = R.o.method == TT_METHOD_TWO_TRAINS;
   D.o_pairs = take(two ? sizeof(int2) * (size_t)R.max_jobs / 2 : 0);
   D.o_host = take(sizeof(double) * host_scratch_doubles((size_t)R.o.max_d));
+  D.o_disc = take(sizeof(double) * R.o.max_batch);
   D.stage_bytes = s;
   size_t off = 0;
   auto take2 = [&](size_t bytes) {
@@ -1137,9 +1156,28 @@ int validate_problem(const tt_problem& p, const tt_options& o, double* scr) {
 // shifts delta, linear phase coefficients, log prefactor, sign and weight.
 // Writes the problem's jobs at jobs[nj..] and their parameter blocks at
 // params[poff..]; `scr` holds 8 d doubles.  No heap memory.
-void derive_trains(const tt_problem& p, int i, bool two, JobDesc* jobs, double* params, int2* pairs, int& nj,
-                   int& np, size_t& poff, int* cnt, double* scr) {
+// The rank threshold and block height of a problem: its class's (first match),
+// else the options'.
+void problem_knobs(const Resolved& R, const tt_problem& p, double* theta, int* block_rows) {
+  *theta = R.o.rank_tol;
+  *block_rows = R.o.block_rows;
+  for (int c = 0; c < R.n_classes; ++c) {
+    const tt_class_tuning& t = R.classes[c];
+    if (p.d < t.d_min || p.d > t.d_max || (t.n_grid && t.n_grid != p.n_grid) ||
+        (t.max_rank && t.max_rank != p.max_rank) || (t.payoff >= 0 && t.payoff != p.payoff))
+      continue;
+    if (t.rank_tol > 0) *theta = t.rank_tol;
+    if (t.block_rows >= p.max_rank && t.block_rows > 0) *block_rows = t.block_rows;
+    return;
+  }
+}
+
+void derive_trains(const Resolved& R, const tt_problem& p, int i, bool two, JobDesc* jobs, double* params,
+                   int2* pairs, int& nj, int& np, size_t& poff, int* cnt, double* scr) {
   const int d = p.d;
+  double theta = 0.0;
+  int brows = 0;
+  problem_knobs(R, p, &theta, &brows);
   const double T = p.maturity, K = p.strike, lk = std::log(K);
   const int N = p.n_grid;
   const double eta = 2.0 * p.trunc_L / N;
@@ -1164,6 +1202,8 @@ void derive_trains(const tt_problem& p, int i, bool two, JobDesc* jobs, double* 
     jd.L = p.trunc_L;
     jd.weight = weight;
     jd.cap = cap;
+    jd.theta = theta;
+    jd.block_rows = brows;
     return jd;
   };
   // covariance of max-call term j0's variables y_j0 = x_j0, y_l = x_l - x_j0: A Cov A^T
@@ -1305,6 +1345,22 @@ void derive_trains(const tt_problem& p, int i, bool two, JobDesc* jobs, double* 
   }
 }
 
+// Relative discretisation error of the midpoint grid (Eq. discr) by the
+// Poisson-summation model: axis j aliases at rate a_j (delta_j for the call on
+// the minimum; |alpha_j| for the maximum, on its maximum's axis delta - 1) with
+// a relative term exp(-2 pi a_j / eta), and the cut Gaussian tail adds
+// exp(-T sigma_j^2 L^2 / 2).  Multiplied by the price at the end.
+double disc_factor(const tt_problem& p) {
+  const double eta = 2.0 * p.trunc_L / p.n_grid;
+  double f = 0.0;
+  for (int j = 0; j < p.d; ++j) {
+    const double a = p.payoff == TT_MIN_CALL ? -p.damping[j] : std::fabs(p.damping[j]);
+    f += std::exp(-2.0 * M_PI * a / eta);
+    f += std::exp(-0.5 * p.maturity * p.cov[j * p.d + j] * p.trunc_L * p.trunc_L);
+  }
+  return f;
+}
+
 // Queue cost of a job (largest first): its fiber work d N r^2.
 double job_cost(const JobDesc& q) {
   return (double)std::max(q.d - 1, 1) * q.n * (double)q.rmax * q.rmax * (q.d > 1 ? 1.0 : 0.01);
@@ -1326,6 +1382,7 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   int* hstat = reinterpret_cast<int*>(st + h->dl.o_hstatus);
   int2* pairs = reinterpret_cast<int2*>(st + h->dl.o_pairs);
   double* scr = reinterpret_cast<double*>(st + h->dl.o_host);
+  double* disc = reinterpret_cast<double*>(st + h->dl.o_disc);
   const bool two = o.method == TT_METHOD_TWO_TRAINS;
   int nj = 0, np = 0;
   size_t poff = 0;
@@ -1333,7 +1390,11 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
     first[i] = nj;
     cnt[i] = 0;
     hstat[i] = validate_problem(probs[i], o, scr);
-    if (hstat[i] == TT_OK) derive_trains(probs[i], i, two, jobs, params, pairs, nj, np, poff, cnt, scr);
+    disc[i] = std::nan("");
+    if (hstat[i] == TT_OK) {
+      derive_trains(h->R, probs[i], i, two, jobs, params, pairs, nj, np, poff, cnt, scr);
+      disc[i] = disc_factor(probs[i]);
+    }
   }
   // largest jobs first, ties by job number (std::sort works in place)
   for (int j = 0; j < nj; ++j) order[j] = j;
@@ -1490,6 +1551,8 @@ int results_impl(tt_pricer* h, double* prices, tt_diag* diag) {
       diag[i].maxvol_rollbacks = r.rollbacks;
       diag[i].imag_part = r.imag;
       diag[i].flops = r.flops;
+      diag[i].est_discretization_err =
+          std::fabs(r.price) * reinterpret_cast<const double*>(h->h_stage + h->dl.o_disc)[i];
     }
     if (r.status < 0 && (worst_err == 0 || r.status < worst_err)) worst_err = r.status;
     if (r.status > worst_warn) worst_warn = r.status;
@@ -1682,7 +1745,8 @@ constexpr size_t kStaticParams = (size_t)kStaticJobs * (TT_STATIC_MAX_D * TT_STA
 constexpr size_t kStaticStageBytes =
     (sizeof(JobDesc) * kStaticJobs + 255) / 256 * 256 + (sizeof(double) * kStaticParams + 255) / 256 * 256 +
     (sizeof(int) * kStaticJobs + 255) / 256 * 256 + 3 * ((sizeof(int) * TT_STATIC_MAX_BATCH + 255) / 256 * 256) +
-    (sizeof(double) * host_scratch_doubles(TT_STATIC_MAX_D) + 255) / 256 * 256;
+    (sizeof(double) * host_scratch_doubles(TT_STATIC_MAX_D) + 255) / 256 * 256 +
+    (sizeof(double) * TT_STATIC_MAX_BATCH + 255) / 256 * 256;
 constexpr int kStaticMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[TT_STATIC_SCRATCH_BYTES];

@@ -362,10 +362,18 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
     if (lane == 0) x.colmax[c] = mx;
   }
   __syncthreads();
-  const bool own = tid < q;
+  // up to 128 candidates: two threads per row, the row's columns split by parity
+  // (the half holding column c + 1 offers the row for the next pivot); more: one
+  // thread per row
+  static_assert(kThreads == 256, "two threads per row: tid >> 7 picks the half");
+  const bool split = q <= kThreads / 2;
+  const int row = split ? (tid & (kThreads / 2 - 1)) : tid;
+  const int half = split ? (tid >> 7) : 0;
+  const int js = split ? 2 : 1;
+  const bool own = row < q;
   bool mine_used = false;
-  R v = own ? cabs2(S[tid]) : R(-1);
-  int vi = own ? tid : INT_MAX;
+  R v = (own && half == 0) ? cabs2(S[row]) : R(-1);
+  int vi = (own && half == 0) ? row : INT_MAX;
   int buf = 0;
   block_argmax(v, vi, x.redv, x.redi, buf);
   int nsel = 0;
@@ -378,36 +386,37 @@ __device__ int gepp_select(Ctx<R>& x, int q, int ncol, int ld, R thr2) {
         x.selr[nsel] = p;
         x.selc[nsel] = c;
       }
-      const bool active = own && !mine_used && tid != p;
-      if (tid == p) mine_used = true;
+      const bool active = own && !mine_used && row != p;
+      if (row == p) mine_used = true;
       if (active && c + 1 < ncol) {
-        const cpx<R> l = cmul(S[c * ld + tid], crecip(S[c * ld + p]));
-        // four columns at a time: loads first, then the updates, so the loads
-        // of a chunk do not wait on the previous chunk's stores
+        const cpx<R> l = cmul(S[c * ld + row], crecip(S[c * ld + p]));
+        // this thread's columns: c + 1 onwards with its parity (split) or all;
+        // four at a time, loads first, then the updates
         int j = c + 1;
-        for (; j + 3 < ncol; j += 4) {
-          cpx<R> a0 = S[j * ld + tid], a1 = S[(j + 1) * ld + tid];
-          cpx<R> a2 = S[(j + 2) * ld + tid], a3 = S[(j + 3) * ld + tid];
-          const cpx<R> p0 = S[j * ld + p], p1 = S[(j + 1) * ld + p];
-          const cpx<R> p2 = S[(j + 2) * ld + p], p3 = S[(j + 3) * ld + p];
+        if (split && ((j & 1) != half)) ++j;
+        for (; j + 3 * js < ncol; j += 4 * js) {
+          cpx<R> a0 = S[j * ld + row], a1 = S[(j + js) * ld + row];
+          cpx<R> a2 = S[(j + 2 * js) * ld + row], a3 = S[(j + 3 * js) * ld + row];
+          const cpx<R> p0 = S[j * ld + p], p1 = S[(j + js) * ld + p];
+          const cpx<R> p2 = S[(j + 2 * js) * ld + p], p3 = S[(j + 3 * js) * ld + p];
           cfms(a0, l, p0);
           cfms(a1, l, p1);
           cfms(a2, l, p2);
           cfms(a3, l, p3);
-          S[j * ld + tid] = a0;
-          S[(j + 1) * ld + tid] = a1;
-          S[(j + 2) * ld + tid] = a2;
-          S[(j + 3) * ld + tid] = a3;
+          S[j * ld + row] = a0;
+          S[(j + js) * ld + row] = a1;
+          S[(j + 2 * js) * ld + row] = a2;
+          S[(j + 3 * js) * ld + row] = a3;
         }
-        for (; j < ncol; ++j) cfms(S[j * ld + tid], l, S[j * ld + p]);
+        for (; j < ncol; j += js) cfms(S[j * ld + row], l, S[j * ld + p]);
       }
       ++nsel;
       if (tid == 0) fl += (long long)(q - nsel) * (ncol - c - 1);
     }
     if (c + 1 < ncol) {
-      const bool active = own && !mine_used;
-      v = active ? cabs2(S[(c + 1) * ld + tid]) : R(-1);
-      vi = active ? tid : INT_MAX;
+      const bool offer = own && !mine_used && (!split || (((c + 1) & 1) == half));
+      v = offer ? cabs2(S[(c + 1) * ld + row]) : R(-1);
+      vi = offer ? row : INT_MAX;
       buf ^= 1;
       block_argmax(v, vi, x.redv, x.redi, buf);
     }
@@ -545,8 +554,9 @@ __device__ __forceinline__ void eval_prow(Ctx<R>& x, int j, int g, int rho) {
 // ---------------------------------------------------------------------------
 // Fibers of more than kScreenMinRows rows are screened: every kScreenBlock rows
 // form one merge, whose candidates are, from each kScreenSub-row sub-block, the
-// kScreenKeep rows with the largest max_c |a_rc|^2 (rounded to FP32; ties to the
-// lower row), in ascending row order.  One warp screens one sub-block.
+// kScreenKeep rows with the largest max_c log|a_rc| (the log-magnitude in the
+// working precision, which needs no complex evaluation; ties to the lower row),
+// in ascending row order.  One warp screens one sub-block.
 constexpr int kScreenMinRows = 512;  // larger fibers offer >= 4 full sub-blocks: 64 candidates
 constexpr int kScreenBlock = 1024;
 constexpr int kScreenSub = 128;
@@ -554,21 +564,49 @@ constexpr int kScreenKeep = 16;
 constexpr int kScreenRpl = kScreenSub / 32;  // rows per lane
 static_assert(kScreenBlock == kWarps * kScreenSub, "one warp per sub-block");
 
+// Warp argmax of a key of either sign (larger wins, then lower index); a lane
+// with no candidate passes valid = false; i = INT_MAX when no lane has one.
+template <typename R>
+__device__ __forceinline__ void warp_argmax_key(R v, int& i, bool valid) {
+  if constexpr (sizeof(R) == 4) {
+    // order-preserving map of the float's bits to unsigned; 0 = no candidate
+    const unsigned u = __float_as_uint(v);
+    const unsigned key = valid ? max(1u, (u & 0x80000000u) ? ~u : (u | 0x80000000u)) : 0u;
+    const unsigned mk = __reduce_max_sync(0xffffffffu, key);
+    const unsigned mi = __reduce_min_sync(0xffffffffu, (key == mk) ? (unsigned)i : 0xffffffffu);
+    i = mk == 0u ? INT_MAX : (int)mi;
+  } else {
+    int bi = valid ? i : INT_MAX;
+    R bv = v;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const R v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (i2 != INT_MAX && (bi == INT_MAX || v2 > bv || (v2 == bv && i2 < bi))) {
+        bv = v2;
+        bi = i2;
+      }
+    }
+    i = bi;
+  }
+}
+
 template <typename R>
 __device__ int screen_block(Ctx<R>& x, int ss, int se, int nc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = x.n;
   const int base = ss + warp * kScreenSub;
-  float key[kScreenRpl];
+  R key[kScreenRpl];
   bool valid[kScreenRpl];
 #pragma unroll
   for (int h = 0; h < kScreenRpl; ++h) {
     const int r = base + lane + 32 * h;
     valid[h] = r < se;
-    key[h] = 0.0f;
+    key[h] = R(0);
     if (valid[h]) {
-      R mx = R(0);
-      for (int c = 0; c < nc; ++c) mx = fmax(mx, cabs2(eval_point_unscaled(x, r / N, r % N, c)));
-      key[h] = (float)mx;
+      R mx = -Num<R>::kHuge;
+      for (int c = 0; c < nc; ++c) mx = fmax(mx, eval_logmag(x, r / N, r % N, c));
+      key[h] = mx;
+      valid[h] = mx == mx;  // a NaN log-magnitude never screens in
     }
   }
   // warp top-kScreenKeep: repeated argmax; the kept set is a row mask, 32 rows per word
@@ -580,12 +618,17 @@ __device__ int screen_block(Ctx<R>& x, int ss, int se, int nc) {
     taken[h] = false;
   }
   for (int t = 0; t < kScreenKeep; ++t) {
-    float v = -1.0f;
+    R v = R(0);
     int vi = INT_MAX;
+    bool any = false;
 #pragma unroll
     for (int h = 0; h < kScreenRpl; ++h)
-      if (valid[h] && !taken[h]) am_merge(v, vi, key[h], lane + 32 * h);
-    warp_argmax(v, vi);
+      if (valid[h] && !taken[h] && (!any || key[h] > v)) {  // rows ascend with h: ties keep the lower
+        v = key[h];
+        vi = lane + 32 * h;
+        any = true;
+      }
+    warp_argmax_key(v, vi, any);
     if (vi == INT_MAX) break;
 #pragma unroll
     for (int h = 0; h < kScreenRpl; ++h)
@@ -618,7 +661,7 @@ __device__ int screen_block(Ctx<R>& x, int ss, int se, int nc) {
   }
   __syncthreads();
   if (sel >= 0) x.scand[tid] = sel;
-  if (tid == 0) x.flops += 24.0 * (double)(se - ss) * nc;
+  if (tid == 0) x.flops += 4.0 * (double)(se - ss) * nc;
   __syncthreads();
   return tot;
 }
@@ -1336,9 +1379,37 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
 // ---------------------------------------------------------------------------
 // contraction step: v <- (v S) P^{-1}, FP64 (Gaussian elimination on P^T)
 // ---------------------------------------------------------------------------
+// block argmax of an FP64 magnitude (larger wins, then lower index); 2 kWarps
+// doubles and ints of scratch per buffer pair
+__device__ __forceinline__ void block_argmax_f64(double& v, int& i, double* rv, int* ri, int buf) {
+  warp_argmax(v, i);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    rv[buf * kWarps + warp] = v;
+    ri[buf * kWarps + warp] = i;
+  }
+  __syncthreads();
+  v = rv[buf * kWarps];
+  i = ri[buf * kWarps];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) am_merge(v, i, rv[buf * kWarps + w], ri[buf * kWarps + w]);
+}
+
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// y P = w by Gaussian elimination with partial pivoting on [P^T | w^T], FP64.
+// Rows stay in place: the pivot of column c is the unused row with the largest
+// |entry|^2 (order[c]); the other unused rows subtract their multiple of it at
+// the columns right of c, tpr threads per row (the row's first thread forms the
+// multiplier and passes it on by shuffle), and the threads holding column c + 1
+// collect its argmax, so an elimination step costs one block barrier.  The pivot
+// row's first thread forms 1/pivot meanwhile, and warp 0 back-substitutes by
+// shuffles alone.
 template <typename R>
 __device__ void chain_solve(Ctx<R>& x, int no, int rho) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int t = tid; t < rho; t += kThreads) {
     double2 y = make_double2(0.0, 0.0);
     for (int o = 0; o < no; ++o) {
@@ -1349,9 +1420,12 @@ __device__ void chain_solve(Ctx<R>& x, int no, int rho) {
     x.ychain[t] = y;
   }
   __syncthreads();
-  // Gaussian elimination with partial pivoting on P^T, FP64
-  double2* G = reinterpret_cast<double2*>(x.sw);  // rho x (rho+1), row-major
+  double2* G = reinterpret_cast<double2*>(x.sw);  // rho x (rho+1), row-major: [P^T | y^T]
   const int lg = rho + 1;
+  double* rv = reinterpret_cast<double*>(G + rho * lg);  // 2 kWarps doubles, then 2 kWarps ints
+  int* ri = reinterpret_cast<int*>(rv + 2 * kWarps);
+  double2* ipiv = reinterpret_cast<double2*>(x.swcol);  // 1/pivot of step c
+  int* order = x.selr;
   for (int idx = tid; idx < rho * lg; idx += kThreads) {
     const int r = idx / lg, c = idx % lg;
     if (c < rho) {
@@ -1362,75 +1436,91 @@ __device__ void chain_solve(Ctx<R>& x, int no, int rho) {
     }
   }
   __syncthreads();
-  double2* fac = reinterpret_cast<double2*>(x.swcol);
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int c = 0; c < rho; ++c) {
-    if (warp == 0) {
-      double v = -1.0;
-      int vi = INT_MAX;
-      for (int r = c + lane; r < rho; r += 32) {
-        const double2 g = G[r * lg + c];
-        am_merge(v, vi, g.x * g.x + g.y * g.y, r);
-      }
-      warp_argmax(v, vi);
-      if (lane == 0) {
-        x.misc[MISC_PIV] = vi;
-        if (!(v > 0.0)) {
-          x.misc[MISC_FAIL] = 1;
-          x.fail_step = 3;
-        }
-      }
-    }
-    __syncthreads();
-    const int p = x.misc[MISC_PIV];
-    if (p != c && p < rho) {
-      for (int j = c + tid; j < lg; j += kThreads) {
-        const double2 t = G[c * lg + j];
-        G[c * lg + j] = G[p * lg + j];
-        G[p * lg + j] = t;
-      }
-    }
-    __syncthreads();
-    {
-      const double2 pv = G[c * lg + c];
-      const double den = pv.x * pv.x + pv.y * pv.y;
-      for (int r = c + 1 + tid; r < rho; r += kThreads) {
-        const double2 g = G[r * lg + c];
-        fac[r] = make_double2((g.x * pv.x + g.y * pv.y) / den, (g.y * pv.x - g.x * pv.y) / den);
-      }
-    }
-    __syncthreads();
-    const int w = lg - c - 1;
-    for (int idx = tid; idx < (rho - c - 1) * w; idx += kThreads) {
-      const int r = c + 1 + idx / w, j = c + 1 + idx % w;
-      const double2 f = fac[r], g = G[c * lg + j];
-      double2& t = G[r * lg + j];
-      t.x -= f.x * g.x - f.y * g.y;
-      t.y -= f.x * g.y + f.y * g.x;
-    }
-    __syncthreads();
+  const int tpr = rho <= 32 ? 8 : 4;  // threads per row (rho <= 64)
+  const int myr = tid / tpr, part = tid % tpr;
+  double v = -1.0;
+  int vi = INT_MAX;
+  if (myr < rho && part == 0) {
+    const double2 g = G[myr * lg];
+    am_merge(v, vi, g.x * g.x + g.y * g.y, myr);
   }
-  if (warp == 0) {
-    for (int r = rho - 1; r >= 0; --r) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int j = r + 1 + lane; j < rho; j += 32) {
-        const double2 g = G[r * lg + j], v = x.vchain[j];
-        s.x += g.x * v.x - g.y * v.y;
-        s.y += g.x * v.y + g.y * v.x;
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
-      }
-      if (lane == 0) {
-        const double2 rhs = G[r * lg + rho], pv = G[r * lg + r];
-        const double nx = rhs.x - s.x, ny = rhs.y - s.y;
-        const double den = pv.x * pv.x + pv.y * pv.y;
-        x.vchain[r] = make_double2((nx * pv.x + ny * pv.y) / den, (ny * pv.x - nx * pv.y) / den);
-      }
-      __syncwarp();
+  int buf = 0;
+  block_argmax_f64(v, vi, rv, ri, buf);
+  unsigned long long used = 0ull;
+  bool ok = true;
+  for (int c = 0; c < rho; ++c) {  // v, vi, used: block-uniform
+    if (!(v > 0.0) || !(v < INFINITY)) {
+      ok = false;
+      break;
     }
+    const int p = vi;
+    if (tid == 0) order[c] = p;
+    used |= 1ull << p;
+    v = -1.0;
+    vi = INT_MAX;
+    const bool active = myr < rho && !((used >> myr) & 1ull);  // unused after this step (p excluded)
+    double2 f = make_double2(0.0, 0.0);
+    if (part == 0 && myr < rho && (active || myr == p)) {
+      // one division on the step's critical path: conj(pivot) / |pivot|^2
+      const double2 pv = G[p * lg + c];
+      const double rd = 1.0 / (pv.x * pv.x + pv.y * pv.y);
+      const double2 ip = make_double2(pv.x * rd, -pv.y * rd);
+      if (active) {
+        f = cmul_d(G[myr * lg + c], ip);
+      } else {
+        ipiv[c] = ip;
+      }
+    }
+    // the row's first thread hands its multiplier to the row's other threads
+    f.x = __shfl_sync(0xffffffffu, f.x, lane & ~(tpr - 1));
+    f.y = __shfl_sync(0xffffffffu, f.y, lane & ~(tpr - 1));
+    if (active) {
+      for (int j = c + 1 + part; j <= rho; j += tpr) {
+        double2 a = G[myr * lg + j];
+        const double2 g = G[p * lg + j];
+        a.x -= f.x * g.x - f.y * g.y;
+        a.y -= f.x * g.y + f.y * g.x;
+        G[myr * lg + j] = a;
+        if (j == c + 1 && j < rho) am_merge(v, vi, a.x * a.x + a.y * a.y, myr);
+      }
+    }
+    buf ^= 1;
+    block_argmax_f64(v, vi, rv, ri, buf);  // its barrier also publishes the updates
+  }
+  if (!ok) {
+    if (tid == 0) {
+      x.misc[MISC_FAIL] = 1;
+      x.fail_step = 3;
+    }
+  } else if (warp == 0) {
+    // back substitution, lane l holding the right-hand side of step l (and l + 32)
+    double2 r0 = lane < rho ? G[order[lane] * lg + rho] : make_double2(0.0, 0.0);
+    double2 r1 = lane + 32 < rho ? G[order[lane + 32] * lg + rho] : make_double2(0.0, 0.0);
+    for (int c = rho - 1; c >= 0; --c) {
+      const bool hi = c >= 32;
+      const int owner = c & 31;
+      double2 xc = make_double2(0.0, 0.0);
+      if (lane == owner) xc = cmul_d(hi ? r1 : r0, ipiv[c]);
+      xc.x = __shfl_sync(0xffffffffu, xc.x, owner);
+      xc.y = __shfl_sync(0xffffffffu, xc.y, owner);
+      if (lane == owner) {
+        if (hi) r1 = xc;
+        else r0 = xc;
+      }
+      // steps before c subtract their coefficient of x_c
+      if (lane < c) {
+        const double2 g = G[order[lane] * lg + c];
+        r0.x -= g.x * xc.x - g.y * xc.y;
+        r0.y -= g.x * xc.y + g.y * xc.x;
+      }
+      if (lane + 32 < c) {
+        const double2 g = G[order[lane + 32] * lg + c];
+        r1.x -= g.x * xc.x - g.y * xc.y;
+        r1.y -= g.x * xc.y + g.y * xc.x;
+      }
+    }
+    if (lane < rho) x.vchain[lane] = r0;
+    if (lane + 32 < rho) x.vchain[lane + 32] = r1;
   }
   if (tid == 0) x.flops += 8.0 * (double)no * rho + 8.0 * (double)rho * rho * rho / 3.0;
   __syncthreads();

@@ -103,6 +103,7 @@ template <typename R> struct Num;
 template <> struct Num<float> {
   static constexpr double kLogScale = 1.4426950408889634;  // log2(e)
   static constexpr bool kScaleColumns = true;  // power-of-two shifts
+  static constexpr float kHuge = 3.0e38f;
   __device__ static __forceinline__ float ex(float e) { return exp2f(e); }
   __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   __device__ static __forceinline__ double unscale(double shift) { return exp2(shift); }
@@ -113,6 +114,7 @@ template <> struct Num<float> {
 template <> struct Num<double> {
   static constexpr double kLogScale = 1.0;
   static constexpr bool kScaleColumns = true;  // power-of-two shifts, as k ln 2
+  static constexpr double kHuge = 1.0e300;
   __device__ static __forceinline__ double ex(double e) { return exp(e); }
   __device__ static __forceinline__ double div(double a, double b) { return a / b; }
   __device__ static __forceinline__ double unscale(double shift) { return exp(shift); }
@@ -141,6 +143,9 @@ struct JobDesc {
   double Tq;      // time factor of the Gaussian exponent -Tq/2 u^T Cov u (0: no Gaussian)
   double logscale, sign, weight;  // true integrand = sign*exp(logscale + sum norms)*value
   double cap;  // no-arbitrage bound on the train's share of the price: the sum of the spots
+  double theta;    // rank threshold of this job (its class's, else the options')
+  int block_rows;  // rows per elimination/maxvol block of this job
+  int pad_;
 };
 
 // Skeleton of a factor train's core k (two-train form), written by the cross at
@@ -415,11 +420,6 @@ __device__ __forceinline__ cpx<R> eval_row_point(const Ctx<R>& x, const RowTab<R
     w = cmul(w, cpx<R>{x.D0, -s});
   }
   return {w.re * f, w.im * f};
-}
-
-template <typename R>
-__device__ __forceinline__ cpx<R> eval_point_unscaled(const Ctx<R>& x, int o, int i, int col) {
-  return eval_point<R, false>(x, o, i, col);
 }
 
 }  // namespace ttp

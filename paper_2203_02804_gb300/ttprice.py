@@ -42,13 +42,24 @@ EXPORTS = ("tt_price_create", "tt_workspace_bytes", "tt_price_evaluate", "tt_pri
            "tt_status_string", "tt_price_evaluate_static",
            # the surrogate's network kernels (include/ttmlp.h)
            "tt_mlp_forward", "tt_mlp_forward_bf16", "tt_mlp_backward", "tt_mlp_mse", "tt_mlp_adam",
-           "tt_mlp_to_bf16", "tt_mlp_ensemble", "tt_mlp_gather")
+           "tt_mlp_to_bf16", "tt_mlp_ensemble", "tt_mlp_gather",
+           # measured arithmetic peaks (include/ttprobe.h)
+           "tt_probe_fma_peak")
 
 # limits of tt_price_evaluate_static (include/ttprice.h)
 TT_STATIC_MAX_BATCH = 64
 TT_STATIC_MAX_D = 8
 TT_STATIC_MAX_N = 256
 TT_STATIC_MAX_RANK = 32
+
+
+class tt_class_tuning(ctypes.Structure):
+    _fields_ = [("d_min", ctypes.c_int), ("d_max", ctypes.c_int), ("n_grid", ctypes.c_int),
+                ("max_rank", ctypes.c_int), ("payoff", ctypes.c_int), ("block_rows", ctypes.c_int),
+                ("rank_tol", ctypes.c_double)]
+
+
+TT_MAX_CLASSES = 64
 
 
 class tt_options(ctypes.Structure):
@@ -59,7 +70,8 @@ class tt_options(ctypes.Structure):
                 ("block_rows", ctypes.c_int), ("engine", ctypes.c_int), ("graph", ctypes.c_int),
                 ("method", ctypes.c_int), ("device", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("classes", ctypes.POINTER(tt_class_tuning)),
+                ("n_classes", ctypes.c_int)]
 
 
 class tt_problem(ctypes.Structure):
@@ -77,7 +89,7 @@ class tt_diag(ctypes.Structure):
                 ("evaluations", ctypes.c_longlong), ("maxvol_swaps", ctypes.c_longlong),
                 ("block_visits", ctypes.c_longlong), ("fail_step", ctypes.c_int),
                 ("maxvol_rollbacks", ctypes.c_int), ("imag_part", ctypes.c_double),
-                ("flops", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("est_discretization_err", ctypes.c_double)]
 
 
 _lib = None
@@ -117,6 +129,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
                                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(tt_diag)]
     lib.tt_price_evaluate_static.restype = ctypes.c_int
+    if hasattr(lib, "tt_probe_fma_peak"):  # absent from single-source profiling builds
+        lib.tt_probe_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        lib.tt_probe_fma_peak.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -124,6 +139,15 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
 
 def status_string(code: int) -> str:
     return load_library().tt_status_string(int(code)).decode()
+
+
+def fma_peak(precision: str, reps: int = 5) -> float:
+    """Measured FMA throughput of the current CUDA device in TFLOP/s (include/ttprobe.h)."""
+    out = ctypes.c_double()
+    rc = load_library().tt_probe_fma_peak(1 if precision == "fp32" else 0, int(reps), ctypes.byref(out))
+    if rc != 0:
+        raise RuntimeError(f"tt_probe_fma_peak failed ({rc})")
+    return float(out.value)
 
 
 @dataclass
@@ -139,6 +163,7 @@ class Diag:
     maxvol_rollbacks: int
     imag_part: float
     flops: float
+    est_discretization_err: float
 
 
 # tt_diag as a NumPy record (same offsets as the C struct)
@@ -226,6 +251,21 @@ class ProblemBatch:
         self.arr = r.ctypes.data_as(ctypes.POINTER(tt_problem))
 
 
+def class_table(classes):
+    """A C array of tt_class_tuning from dicts with keys d_min, d_max, n_grid, max_rank,
+    payoff ("min", "max" or None for either), block_rows and rank_tol (missing: 0)."""
+    if len(classes) > TT_MAX_CLASSES:
+        raise ValueError(f"at most {TT_MAX_CLASSES} classes")
+    arr = (tt_class_tuning * max(1, len(classes)))()
+    for c, src in zip(arr, classes):
+        c.d_min, c.d_max = int(src.get("d_min", 1)), int(src.get("d_max", 255))
+        c.n_grid, c.max_rank = int(src.get("n_grid", 0)), int(src.get("max_rank", 0))
+        pay = src.get("payoff")
+        c.payoff = -1 if pay is None else (TT_MIN_CALL if pay == "min" else TT_MAX_CALL)
+        c.block_rows, c.rank_tol = int(src.get("block_rows", 0)), float(src.get("rank_tol", 0.0))
+    return arr
+
+
 class Pricer:
     """Owns one tt_pricer handle on a CUDA device, with a torch-allocated workspace.
 
@@ -238,7 +278,7 @@ class Pricer:
                  precision: str = "fp64", device: int = 0, stream=None, max_half_sweeps: int = 0,
                  sweep_tol: float = 0.0, rank_tol: float = 0.0, maxvol_tol: float = 0.0,
                  block_rows: int = 0, use_torch_workspace: bool = True, engine: str = "auto",
-                 graph: bool = True, method: str = "single"):
+                 graph: bool = True, method: str = "single", classes=None):
         import torch  # device memory and streams only
 
         if not torch.cuda.is_available():
@@ -257,6 +297,10 @@ class Pricer:
         o.graph = 1 if graph else 0
         o.method = METHODS[method]
         o.device = device
+        # per-class block_rows / rank_tol (the autotuner's table); the library copies it
+        self._classes = class_table(classes or [])
+        o.classes = self._classes
+        o.n_classes = len(classes or [])
         with torch.cuda.device(device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)

@@ -1,5 +1,5 @@
 """The C ABI on the CPU: the library builds for sm_103a, loads, exports every
-function include/ttprice.h and include/ttmlp.h declare, and the ctypes mirrors
+function include/*.h declare, and the ctypes mirrors
 of its structs have the C layout (checked against gcc).  No compute call runs
 here."""
 import ctypes
@@ -15,7 +15,7 @@ from paper_2203_02804_gb300 import build, ttprice
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "ttprice.h")
-HEADERS = [HEADER, os.path.join(ROOT, "include", "ttmlp.h")]
+HEADERS = [HEADER, os.path.join(ROOT, "include", "ttmlp.h"), os.path.join(ROOT, "include", "ttprobe.h")]
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +68,26 @@ def test_create_rejects_bad_options_without_touching_the_gpu(lib):
     assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
     o.method, o.max_rank, o.block_rows = ttprice.TT_METHOD_TWO_TRAINS, 64, 128
     assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    # the per-class table: too many classes, a missing table, a class block taller than the options'
+    o.method, o.max_rank, o.block_rows, o.engine = ttprice.TT_METHOD_SINGLE_TRAIN, 16, 64, ttprice.TT_ENGINE_AUTO
+    o.max_d = 4
+    tbl = ttprice.class_table([{"max_rank": 16, "block_rows": 128}])
+    o.classes, o.n_classes = tbl, 1
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    o.n_classes = ttprice.TT_MAX_CLASSES + 1
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    o.classes, o.n_classes = None, 1
+    assert lib.tt_price_create(ctypes.byref(o), ctypes.byref(h)) == ttprice.TT_ERR_INVALID
+    assert not h.value
     lib.tt_price_destroy(None)
+
+
+def test_class_table_marshalling():
+    t = ttprice.class_table([{"d_min": 3, "d_max": 6, "n_grid": 128, "max_rank": 32, "payoff": "max",
+                              "block_rows": 64, "rank_tol": 3e-6}, {"max_rank": 8}])
+    assert (t[0].d_min, t[0].d_max, t[0].n_grid, t[0].max_rank) == (3, 6, 128, 32)
+    assert t[0].payoff == ttprice.TT_MAX_CALL and t[0].block_rows == 64 and t[0].rank_tol == 3e-6
+    assert t[1].payoff == -1 and (t[1].d_min, t[1].d_max) == (1, 255) and t[1].block_rows == 0
 
 
 def test_struct_layouts_match_c():
@@ -83,8 +102,10 @@ def test_struct_layouts_match_c():
              offsetof(tt_options, workspace_bytes));
       printf("%zu %zu %zu %zu %zu\n", sizeof(tt_problem), offsetof(tt_problem, rate),
              offsetof(tt_problem, damping), offsetof(tt_problem, trunc_L), offsetof(tt_problem, seed));
-      printf("%zu %zu %zu %zu\n", sizeof(tt_diag), offsetof(tt_diag, evaluations), offsetof(tt_diag, fail_step),
-             offsetof(tt_diag, flops));
+      printf("%zu %zu %zu %zu %zu\n", sizeof(tt_diag), offsetof(tt_diag, evaluations), offsetof(tt_diag, fail_step),
+             offsetof(tt_diag, flops), offsetof(tt_diag, est_discretization_err));
+      printf("%zu %zu %zu\n", sizeof(tt_class_tuning), offsetof(tt_class_tuning, rank_tol),
+             offsetof(tt_options, n_classes));
       return 0;
     }
     """
@@ -102,8 +123,10 @@ def test_struct_layouts_match_c():
         [ctypes.sizeof(T.tt_problem), T.tt_problem.rate.offset, T.tt_problem.damping.offset,
          T.tt_problem.trunc_L.offset, T.tt_problem.seed.offset],
         [ctypes.sizeof(T.tt_diag), T.tt_diag.evaluations.offset, T.tt_diag.fail_step.offset,
-         T.tt_diag.flops.offset],
+         T.tt_diag.flops.offset, T.tt_diag.est_discretization_err.offset],
+        [ctypes.sizeof(T.tt_class_tuning), T.tt_class_tuning.rank_tol.offset, T.tt_options.n_classes.offset],
     ]
+    assert len([ln for ln in out if ln.strip()]) == len(want)
     for line, w in zip(out, want):
         assert [int(v) for v in line.split()] == w
 

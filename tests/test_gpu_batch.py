@@ -1,25 +1,38 @@
 """The heterogeneous batch at full size: 4096 problems of uneven d, N and rank,
 calls on the minimum and on the maximum mixed 50/50, in one launch.
 
-The whole batch runs in the launch configuration the library uses for any batch;
-sampled problems are checked against the FP64 oracle one by one (the mixed path
-to 1e-4, the FP64 path to 1e-6), and every price is checked for the properties
-that hold at any size: a finite positive price, a status that is OK or
-not-converged, and an imaginary part of the grid sum that is small next to the
-price (the midpoint grid is symmetric, so the exact grid sum is real and the
-imaginary part is TT error).  Many draws cap the rank below what the integrand
-needs (rank 8 at d = 10); their sweeps end unconverged with a TT error of up to
-tens of percent in either precision, so the tight bound on the imaginary part
-applies to converged problems and the loose one only rules out a blow-up."""
+The whole batch runs in the launch configuration the library uses for any batch.
+Every price is checked for the properties that hold at any size: a finite
+positive price, a status that is OK or not-converged, and an imaginary part of
+the grid sum that is small next to the price (the midpoint grid is symmetric, so
+the exact grid sum is real and the imaginary part is TT error).  Many draws cap
+the rank below what the integrand needs (rank 8 at d = 10); their sweeps end
+unconverged with a TT error of up to tens of percent in either precision, so the
+tight bound on the imaginary part applies to converged problems and the loose
+one only rules out a blow-up.
+
+Parity is checked element by element on a stratified sample: one problem per
+(d, N, payoff) cell whose FP64 oracle train has converged, with the oracle's
+prices stored in tests/golden/hetero_stratified.json by
+tests/golden/make_hetero_golden.py (which calls only the oracle).  First-tier
+cells (oracle within 1e-7 of the exact grid sum, or, for the call on the
+maximum, every term's stop rule held with an imaginary part below 1e-7) are
+held to 1e-6 in FP64 and 1e-4 in the mixed path; second-tier cells (error
+measure below 1e-5) to 1e-4 in the mixed path.  The mixed bound carries the
+FP32 floor of 2e-7 times the spot: the integrand's terms are of the spot's size,
+so single-precision sums leave that much absolute error on prices far below it."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
 
-from oracle import ttcross
 from paper_2203_02804_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hetero_stratified.json")
 
 
 @pytest.fixture(scope="module")
@@ -50,6 +63,16 @@ def _run(tp, problems, precision, engine="auto"):
     return rc, prices, diags
 
 
+def _golden():
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    return g["cells"], g.get("cells_tier2", [])
+
+
+def _mixed_ok(price, ref, p):
+    return abs(price - ref) < 1e-4 * abs(ref) + 2e-7 * float(np.max(p.spot))
+
+
 @pytest.mark.parametrize("engine", ["cuda", "tc"])
 def test_full_heterogeneous_batch_mixed(tp, batch, engine):
     rc, prices, diags = _run(tp, batch, "mixed", engine)
@@ -61,38 +84,27 @@ def test_full_heterogeneous_batch_mixed(tp, batch, engine):
     assert np.all(imag[ok] <= 1e-2 * prices[ok])
     assert np.all(imag <= 0.5 * prices)
     assert sum(d.terms for d in diags) == sum(p.d if p.payoff == "max" else 1 for p in batch)
-    # sampled parity: the cheapest rank-32 problems of each payoff whose FP64
-    # oracle sweep converges (then the train's own error is small, so FP32 pivot
-    # choices that part from FP64 at near-ties stay inside 1e-4; an unconverged,
-    # rank-limited train moves by its TT error with any pivot change), priced one
-    # by one by the oracle
-    for payoff in ("min", "max"):
-        idx = sorted((i for i, p in enumerate(batch) if p.payoff == payoff and p.max_rank == 32),
-                     key=lambda i: _cost(batch[i]))
-        checked = 0
-        for i in idx[:12]:
-            ref, _, odiags = ttcross.tt_price(batch[i])
-            if not all(dg.converged for dg in odiags):
-                continue
-            # 1e-4 relative, with the FP32 floor: the integrand's terms are of the
-            # spot's size, so single-precision arithmetic leaves ~1e-7 x S0 absolute
-            # (a price at 7e-4 of the spot sees it as 1.8e-4 relative)
-            s0 = float(np.max(batch[i].spot))
-            assert abs(prices[i] - ref) < 1e-4 * abs(ref) + 2e-7 * s0, (payoff, i)
-            checked += 1
-            if checked == 3:
-                break
-        assert checked == 3, payoff
+    # the stratified sample, priced inside this one launch of 4096
+    tier1, tier2 = _golden()
+    assert len(tier1) >= 12
+    for c in tier1 + tier2:
+        i = c["index"]
+        assert _mixed_ok(prices[i], c["oracle"], batch[i]), (engine, c["d"], c["n_grid"], c["payoff"], i,
+                                                             prices[i], c["oracle"])
 
 
-def test_heterogeneous_subset_fp64(tp, batch):
-    idx = sorted(range(len(batch)), key=lambda i: _cost(batch[i]))[:8]
-    sub = [batch[i] for i in idx]
+def test_stratified_sample_fp64(tp, batch):
+    """The first-tier cells in FP64 (one launch of the sample, in the full batch's
+    launch configuration): 1e-6 against the oracle."""
+    tier1, _ = _golden()
+    sub = [batch[c["index"]] for c in tier1]
     rc, prices, diags = _run(tp, sub, "fp64")
-    for p, v, dg in zip(sub, prices, diags):
+    for c, v, dg in zip(tier1, prices, diags):
         assert dg.status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
-        ref, _, _ = ttcross.tt_price(p)
-        assert math.isfinite(v) and abs(v / ref - 1) < 1e-6
+        assert math.isfinite(v) and abs(v / c["oracle"] - 1) < 1e-6, (c["d"], c["n_grid"], c["payoff"], v,
+                                                                       c["oracle"])
+        if "exact_grid" in c:
+            assert abs(v / c["exact_grid"] - 1) < 1e-6
 
 
 @pytest.mark.parametrize("engine", ["cuda", "tc"])

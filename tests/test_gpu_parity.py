@@ -293,3 +293,19 @@ def test_mixed_default_rank_tol_at_the_paper_setting(tp):
     pr.close()
     assert all(d.status == tp.TT_OK for d in diags)
     assert max(abs(a / b - 1) for a, b in zip(got, ref)) < 1e-4
+
+
+def test_discretisation_error_estimate(tp):
+    """tt_diag.est_discretization_err against the grid's actual error (the exact grid
+    sum against the one-factor integral) on the d=5 workload at N = 64, 96, 128 and
+    the d=2 workload: within a factor 3 where aliasing dominates, as the
+    Poisson-summation model predicts."""
+    ps = [inputs.five_asset_batch(1)[0].with_(n_grid=n) for n in (64, 96, 128)]
+    ps.append(inputs.two_asset_min_call(n_grid=64, max_rank=32))
+    rc, prices, diags = gpu_price(tp, ps, precision="fp64")
+    for p, v, dg in zip(ps, prices, diags):
+        sig = np.sqrt(np.diag(p.cov))
+        rho = float(p.cov[0, 1] / (sig[0] * sig[1]))
+        exact = closed_forms.one_factor_price(p.spot, sig, rho, p.strike, p.rate, p.maturity, "min")
+        actual = abs(grid_sum.grid_sum_for(p)[0] - exact)
+        assert actual / 3 < dg.est_discretization_err < 3 * actual, (p.d, p.n_grid, dg.est_discretization_err, actual)
