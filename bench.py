@@ -252,6 +252,7 @@ def measure_surrogate(args, tuned):
     s.fit(train_ps, y_train, epochs=args.surrogate_epochs, batch=1024)
     torch.cuda.synchronize()
     fit_s = time.perf_counter() - t0
+    out_warm = measure_warm_start(train_ps[:8192], held[:1024], s.fx)
     mean, spread = s.predict_log(held)
     k = np.array([p.strike for p in held])
     err = np.abs(k * np.exp(mean) / y_held - 1.0)
@@ -262,20 +263,61 @@ def measure_surrogate(args, tuned):
         served = spread <= tol
         out[f"served_at_{tol:g}"] = float(served.mean())
         out[f"max_err_served_{tol:g}"] = float(err[served].max()) if served.any() else None
-    x = s.standardise(held)
-    x = x.repeat(64, 1).contiguous()  # 262,144 quotes
-    for _ in range(2):
-        s.predict_device(x)
     st = s.nets[0].stream
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
     reps = 5
-    for _ in range(reps):
-        s.predict_device(x)
-    b.record(st)
-    torch.cuda.synchronize()
-    out["quotes_per_s"] = reps * x.shape[0] / (a.elapsed_time(b) / 1e3)
-    out["unit"] = "quotes/s (ensemble of 4, bfloat16 weights, features resident)"
+    for key, x in (("quotes_per_s", s.standardise_tc(held)), ("quotes_per_s_fp32_activations", s.standardise(held))):
+        x = x.repeat(64, 1).contiguous()  # 262,144 quotes
+        for _ in range(2):
+            s.predict_device(x)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            s.predict_device(x)
+        b.record(st)
+        torch.cuda.synchronize()
+        out[key] = reps * x.shape[0] / (a.elapsed_time(b) / 1e3)
+    out["unit"] = ("quotes/s (ensemble of 4, features resident): hidden layers on the tensor cores "
+                   "(bfloat16 weights and activations); the other figure on CUDA cores, FP32 activations")
+    out["warm_start"] = out_warm
+    return out
+
+
+def measure_warm_start(train_ps, held, fx):
+    """TT fallback warm-started from the pivots of the nearest training problem in the
+    surrogate's feature space (surrogate.PivotMemory) against the cold start, on
+    held-out problems: half-sweeps, evaluations and device time per precision, and
+    how far the warm prices are from the cold ones (both are trains of one tensor)."""
+    import torch
+
+    from paper_2203_02804_gb300 import surrogate as sg, ttprice
+
+    out = {"memory": len(train_ps), "held_out": len(held)}
+    for prec in ("fp64", "mixed"):
+        pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=max(len(train_ps), len(held)),
+                            precision=prec, pivot_io=True, graph=False)
+        pr.evaluate(train_ps)
+        recs = [pr.pivots(i) for i in range(len(train_ps))]
+        mem = sg.PivotMemory(train_ps, recs, fx)
+        warm = mem.warm(held)
+        res = {}
+        for label, batch in (("cold", held), ("warm", warm)):
+            pr.prepare(batch)
+            pr.run()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(pr.stream)
+            pr.run()
+            b.record(pr.stream)
+            torch.cuda.synchronize()
+            _, v, dg = pr.results()
+            res[label] = {"half_sweeps_mean": float(np.mean([d.half_sweeps for d in dg])),
+                          "evaluations_mean": float(np.mean([d.evaluations for d in dg])),
+                          "not_converged": int(sum(d.status == 1 for d in dg)),
+                          "prices_per_s": len(batch) / (a.elapsed_time(b) / 1e3), "_v": v}
+        pr.close()
+        vc, vw = res["cold"].pop("_v"), res["warm"].pop("_v")
+        res["max_rel_diff_warm_vs_cold"] = float(np.max(np.abs(vw / vc - 1.0)))
+        out[prec] = res
     return out
 
 
@@ -477,13 +519,16 @@ def run_gpu(args):
     # launch configuration from the project's autotuner (untimed; measured on this GPU
     # for the workload's shape), else the library defaults
     tuned = {}
-    if args.engine != "auto":  # a fixed engine (profiling one engine); no tuning
-        tuned = {"engine": args.engine}
+    tuning_records = None
+    if args.engine != "auto" or args.rank_tol > 0:  # fixed knobs (profiling one configuration); no tuning
+        tuned = {k: v for k, v in (("engine", args.engine), ("rank_tol", args.rank_tol)) if v not in ("auto", 0.0)}
     elif not args.no_tune:
         from paper_2203_02804_gb300 import autotune
 
-        entry = autotune.tune(args.precision, 5, 128, 32, "min")
+        entry = autotune.tune(args.precision, 5, 128, 32, "min", count=args.batch)
         tuned = {k: entry[k] for k in autotune.KNOBS}
+        tuning_records = [{k: r[k] for k in ("block_rows", "engine", "rank_tol", "seconds", "agrees")}
+                          for r in entry["records"]]
     pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=args.batch,
                         precision=args.precision, device=local, stream=stream, graph=True, **tuned)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -550,7 +595,7 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": dict(workload_config(args.batch, args.precision), launch="cuda-graph",
-                           tuned=tuned or "defaults"),
+                           tuned=tuned or "defaults", tuning_records=tuning_records),
             "roofline": {"bound": "alu", "achieved": achieved,
                          "peak": peak32 if args.precision == "mixed" else peak64,
                          "unit": "TFLOP/s",
@@ -619,9 +664,11 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--engine", choices=["auto", "cuda", "tc"], default="auto",
                     help="maxvol block-product engine; other than auto it replaces the autotuner's choice")
-    ap.add_argument("--surrogate-samples", type=int, default=1 << 18,
+    ap.add_argument("--surrogate-samples", type=int, default=1 << 20,
                     help="TT-priced training samples of the learned surrogate (0: skip it)")
-    ap.add_argument("--surrogate-epochs", type=int, default=40)
+    ap.add_argument("--surrogate-epochs", type=int, default=10)
+    ap.add_argument("--rank-tol", type=float, default=0.0,
+                    help="fixed rank threshold (with --engine: profile one configuration, no tuning)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="timed steps of the plain FP64 path on the same batch (0: skip)")
     ap.add_argument("--hetero-batch", type=int, default=4096,

@@ -36,6 +36,15 @@ int tt_mlp_forward(const float* x, int batch, int in, const float* w, const floa
 int tt_mlp_forward_bf16(const float* x, int batch, int in, const uint16_t* w_bf16, const float* b, int out,
                         int act, float* z, float* a, void* stream);
 
+/* Inference layer on the tensor cores (tcgen05.mma kind::f16): a = act(x W^T + b)
+ * with x [batch][in] and W [out][in] in bfloat16 and FP32 accumulation; writes a
+ * as FP32 (a, nullable) and/or rounded to bfloat16 (a_bf16, nullable; the next
+ * layer's input).  Needs in and out multiples of 16, 16..256 (pad the input with
+ * zero columns, W with zero columns to match).  A tile whose completion wait runs
+ * out of its bound gets NaN. */
+int tt_mlp_forward_tc(const uint16_t* x_bf16, int batch, int in, const uint16_t* w_bf16, const float* b, int out,
+                      int act, float* a, uint16_t* a_bf16, void* stream);
+
 /* Backward of one layer: g = da * act'(z) (da for TT_MLP_LINEAR), written over da
  * (da holds dL/da on entry and dL/dz on return); dw = g^T x and db = column sums
  * of g (both overwritten); dx = g W when dx != NULL. */

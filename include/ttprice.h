@@ -66,7 +66,10 @@ typedef enum { TT_ENGINE_AUTO = 0, TT_ENGINE_CUDA_CORES = 1, TT_ENGINE_TENSOR_CO
  * right-to-left, left-to-right, the train being the last one's cores; no
  * sum-based stop) and the two trains are contracted site by site,
  * E <- sum_i G^v_k(i)^T E G^phi_k(i), in FP64 in both precisions (TT_MIXED
- * runs the two crosses in FP32).  Needs max_rank <= 32 and max_n <= 1024. */
+ * runs the two crosses in FP32).  The two trains have their own bond
+ * dimensions (tt_problem.max_rank and max_rank_phi, the paper's D_v and D_phi).
+ * Needs max_rank <= 40 and the bracket's shared memory within the SM's
+ * (max_n <= 1024 up to rank 32, about 512 at rank 40). */
 typedef enum { TT_METHOD_SINGLE_TRAIN = 0, TT_METHOD_TWO_TRAINS = 1 } tt_method;
 
 /* Per-class launch configuration (the autotuner's output): problems with
@@ -123,6 +126,9 @@ typedef struct {
   const tt_class_tuning* classes; /* optional per-class block_rows / rank_tol, read
                            (copied) by tt_price_create; NULL = none              */
   int n_classes;        /* entries of classes (0..TT_MAX_CLASSES)                  */
+  int pivot_io;         /* 1: keep every train's final pivots for tt_price_pivots
+                           and accept tt_problem.warm_sets (device memory of
+                           tt_pivot_record_entries() per train, twice); 0: neither */
 } tt_options;
 
 typedef struct {
@@ -141,6 +147,20 @@ typedef struct {
   double trunc_L;        /* L > 0                                                  */
   int max_rank;          /* TT rank cap for this problem (<= tt_options.max_rank)  */
   unsigned long long seed; /* initial random pivots (SplitMix64), per problem       */
+  int max_rank_phi;      /* two-train form only: bond dimension D_phi of the
+                            characteristic function's train (0: max_rank); the
+                            payoff transform's train takes max_rank (D_v).  Needs
+                            max_rank * max_rank_phi <= 1024, else TT_ERR_CAPACITY */
+  const unsigned short* warm_sets; /* optional warm start (needs pivot_io): initial
+                            right index sets of TT-cross (Section IV.B starts from
+                            column sets J_k, at random by default), for each train
+                            of the problem in turn (1 or d terms, single-train
+                            form), in the format tt_price_pivots writes: for
+                            k = 1..d-1 a count c_k, then c_k distinct multi-indices
+                            of grid points over axes k..d-1 (d-k entries each, each
+                            < n_grid).  The first min(c_k, r_k) take the first slots
+                            of bond k; the rest are drawn as usual.  NULL = none;
+                            bad data gives TT_ERR_INVALID for the problem        */
 } tt_problem;
 
 typedef struct {
@@ -248,6 +268,18 @@ int tt_price_transfer_bytes(const tt_pricer* h, size_t* h2d, size_t* d2h);
 #define TT_STATIC_SCRATCH_BYTES (16u << 20)
 int tt_price_evaluate_static(const tt_problem* probs, int count, int precision, void* cuda_stream,
                              double* prices, tt_diag* diag);
+
+/* The final right index sets of problem `problem` of the last run (every train
+ * in turn, in the warm_sets format above; after the last right-to-left
+ * half-sweep, or the initial sets when none ran), for warm-starting a later
+ * solve of a nearby problem.  Needs tt_options.pivot_io.  Copies to the host
+ * and waits.  Returns the number of entries written (<= cap), or a negative
+ * tt_status (TT_ERR_CAPACITY when cap is too small). */
+int tt_price_pivots(tt_pricer* h, int problem, unsigned short* out, size_t cap);
+
+/* Entries of one train's pivot record for problems up to max_d assets and rank
+ * max_rank: (max_d - 1) counts and max_rank (d - k) indices per bond k. */
+size_t tt_pivot_record_entries(int max_d, int max_rank);
 
 /* Release everything the handle owns.  NULL-safe. */
 void tt_price_destroy(tt_pricer* h);

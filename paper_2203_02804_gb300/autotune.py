@@ -162,15 +162,20 @@ def gpu_measure(precision: str, batch: Sequence, reps: int = 3, classes=None):
 
 
 def tune(precision: str, d: int, n: int, rank: int, payoff: str = "min", path: Optional[str] = None,
-         measure: Optional[Callable] = None, reference: Optional[np.ndarray] = None) -> dict:
-    """Tune one shape on a seeded batch of three persistent waves; cache the winner."""
+         measure: Optional[Callable] = None, reference: Optional[np.ndarray] = None,
+         count: Optional[int] = None) -> dict:
+    """Tune one shape on a seeded batch (`count` problems, default three persistent
+    waves; the batch size the caller will run is the representative choice, since
+    the tail of the last wave weighs differently); cache the winner."""
     import torch
 
     from . import inputs
 
     cc = "%d%d" % torch.cuda.get_device_capability(0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    batch = inputs.tuning_batch(3 * 3 * sms if d <= 10 else sms, d, n, rank, payoff)
+    if count is None:
+        count = 3 * 3 * sms if d <= 10 else sms
+    batch = inputs.tuning_batch(count, d, n, rank, payoff)
     mask = None
     if measure is None:
         measure, ref_fn = gpu_measure(precision, batch)

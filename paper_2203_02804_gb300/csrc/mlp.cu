@@ -1,13 +1,15 @@
 // Kernels of the learned surrogate (include/ttmlp.h): tiled FP32 GEMMs for the
 // fully connected layers (weights in FP32 or bfloat16, products accumulated in
 // FP32), SiLU and its derivative fused into the epilogues, Adam, MSE and the
-// ensemble statistics.
+// ensemble statistics; and the inference layer on the 5th-generation tensor
+// cores (tcgen05.mma kind::f16, bfloat16 operands, FP32 accumulator in TMEM).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "ttmlp.h"
+#include "ttprice_tc.cuh"
 
 namespace ttm {
 
@@ -156,6 +158,101 @@ __global__ void gather_kernel(const float* __restrict__ src, const int* __restri
   dst[i] = src[(long)idx[r] * cols + c];
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core layer: Y = act(X W^T + b), X [M][K] and W [N][K] bfloat16 (both
+// K-major, as stored), 16 <= N <= 256 and K <= 256 multiples of 16.  One CTA of
+// four warps takes 128 rows: X's rows and all of W are staged in shared memory
+// in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices,
+// 128 bytes apart along K, 8-row groups (K/8) 128 bytes apart), one thread
+// issues K/16 MMAs of M = 128, N, K = 16 into TMEM and commits them to an
+// mbarrier, and each warp reads back its 32 TMEM lanes (rows) to add the bias,
+// apply the activation and store FP32 and/or bfloat16 rows.  A completion wait
+// that runs out of its bound leaves NaN in the tile's outputs; the wait before
+// the tensor memory is freed keeps the full bound.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;
+constexpr int kTcThreads = 128;
+
+__device__ __forceinline__ uint32_t f16_idesc(int n) {
+  // D FP32 (bits 4-5 = 1), A and B bfloat16 (bits 7-9 = 1, 10-12 = 1), both
+  // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// 16-byte chunk c (8 bfloat16 along K) of row r into the K-major layout
+__device__ __forceinline__ uint32_t kmaj16(int r, int c, int sbo) { return (r >> 3) * sbo + c * 128 + (r & 7) * 16; }
+
+__global__ void __launch_bounds__(kTcThreads, 1) tc_layer_kernel(const uint16_t* __restrict__ X, int M, int K,
+                                                                  const uint16_t* __restrict__ W, const float* bias,
+                                                                  int N, int act, float* Yf, uint16_t* Yb) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * kTcRows;
+  const int sbo = (K / 8) * 128;
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + (size_t)kTcRows * K * 2;
+  uint32_t ncols = 32;
+  while ((int)ncols < N) ncols <<= 1;
+  if (warp == 0) ttp::tc::tmem_alloc(&tslot, ncols);
+  const int kc = K / 8;
+  for (int idx = tid; idx < kTcRows * kc; idx += kTcThreads) {
+    const int r = idx / kc, c = idx % kc;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (m0 + r < M) v = *reinterpret_cast<const uint4*>(X + (size_t)(m0 + r) * K + c * 8);
+    *reinterpret_cast<uint4*>(sA + kmaj16(r, c, sbo)) = v;
+  }
+  for (int idx = tid; idx < N * kc; idx += kTcThreads) {
+    const int r = idx / kc, c = idx % kc;
+    *reinterpret_cast<uint4*>(sB + kmaj16(r, c, sbo)) = *reinterpret_cast<const uint4*>(W + (size_t)r * K + c * 8);
+  }
+  if (tid == 0) ttp::tc::mbar_init(&mbar, 1);
+  ttp::tc::fence_async_smem();  // the operands were written by the generic proxy
+  ttp::tc::fence_before_sync();
+  __syncthreads();
+  ttp::tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint32_t id = f16_idesc(N);
+    for (int ks = 0; ks < K / 16; ++ks) {  // K = 16 per instruction: two core matrices, 256 bytes
+      const uint64_t a = ttp::tc::smem_desc(ttp::tc::smem_u32(sA) + ks * 256, (uint32_t)sbo);
+      const uint64_t b = ttp::tc::smem_desc(ttp::tc::smem_u32(sB) + ks * 256, (uint32_t)sbo);
+      mma_f16(tmem, a, b, id, ks > 0 ? 1u : 0u);
+    }
+    ttp::tc::commit(&mbar);
+  }
+  const bool done = ttp::tc::mbar_wait(&mbar, 0);
+  ttp::tc::fence_after_sync();
+  const int row = m0 + 32 * warp + lane;
+  for (int c0 = 0; c0 < N; c0 += 8) {
+    float v[8];
+    ttp::tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+    ttp::tc::tmem_wait_ld();
+    if (row < M) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float z = done ? v[c] + (bias ? bias[c0 + c] : 0.0f) : __int_as_float(0x7fc00000);
+        if (act == TT_MLP_SILU) z = silu(z);
+        if (Yf) Yf[(size_t)row * N + c0 + c] = z;
+        if (Yb) Yb[(size_t)row * N + c0 + c] = __bfloat16_as_ushort(__float2bfloat16_rn(z));
+      }
+    }
+  }
+  if (!done) ttp::tc::mbar_wait(&mbar, 0);  // no product in flight when the columns are freed
+  ttp::tc::fence_before_sync();
+  __syncthreads();
+  ttp::tc::fence_after_sync();
+  if (warp == 0) ttp::tc::tmem_dealloc(tmem, ncols);
+}
+
 template <typename TB>
 int gemm(int M, int N, int K, const float* A, long sam, long sak, const TB* B, long sbk, long sbn, float* C,
          long ldc, const float* bias, int act, float* Aout, cudaStream_t st) {
@@ -183,6 +280,22 @@ extern "C" int tt_mlp_forward_bf16(const float* x, int batch, int in, const uint
   if (!x || !w_bf16 || !z || !a || batch < 0 || in < 1 || out < 1) return TT_MLP_INVALID;
   const __nv_bfloat16* w = reinterpret_cast<const __nv_bfloat16*>(w_bf16);
   return gemm<__nv_bfloat16>(batch, out, in, x, in, 1, w, 1, in, z, out, b, act, a, (cudaStream_t)stream);
+}
+
+extern "C" int tt_mlp_forward_tc(const uint16_t* x_bf16, int batch, int in, const uint16_t* w_bf16, const float* b,
+                                 int out, int act, float* a, uint16_t* a_bf16, void* stream) {
+  if (!x_bf16 || !w_bf16 || (!a && !a_bf16) || batch < 0 || in < 16 || in > 256 || in % 16 || out < 16 ||
+      out > 256 || out % 16)
+    return TT_MLP_INVALID;
+  if (batch == 0) return TT_MLP_OK;
+  const int smem = (kTcRows + out) * in * 2;
+  if (cudaFuncSetAttribute(tc_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return TT_MLP_CUDA;
+  }
+  tc_layer_kernel<<<(batch + kTcRows - 1) / kTcRows, kTcThreads, smem, (cudaStream_t)stream>>>(
+      x_bf16, batch, in, w_bf16, b, out, act, a, a_bf16);
+  return cudaGetLastError() == cudaSuccess ? TT_MLP_OK : TT_MLP_CUDA;
 }
 
 extern "C" int tt_mlp_backward(const float* x, const float* z, float* da, int batch, int in, const float* w,

@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
                                                             const int* __restrict__ order, int njobs,
                                                             int* counter, JobResult* results,
                                                             char* scratch, Layout lay, SmemLayout sl,
-                                                            Knobs kn, char* emit, size_t emit_stride) {
+                                                            Knobs kn, char* emit, size_t emit_stride,
+                                                            const uint16_t* __restrict__ warm_buf,
+                                                            uint16_t* piv_out, int pstride) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double dscr[32];
   __shared__ SweepState ss;
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
   x.sacc = reinterpret_cast<double2*>(base + lay.sacc);
   x.vchain = reinterpret_cast<double2*>(base + lay.chain);
   x.ychain = x.vchain + lay.rmax;
+  x.cb = reinterpret_cast<float*>(base + lay.cb);
   x.sw = reinterpret_cast<cpx<R>*>(smem + sl.sw);
   x.M = reinterpret_cast<cpx<R>*>(smem + sl.m);
   x.wvals = reinterpret_cast<cpx<R>*>(smem + sl.wvals);
@@ -148,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       x.D0 = (R)jd.D0;
       x.T = jd.Tq;
       x.emit = jd.factor != FACTOR_PRODUCT ? emit + (size_t)jid * emit_stride : nullptr;
+      x.warm = (warm_buf && jd.warm_off >= 0) ? warm_buf + jd.warm_off : nullptr;
       x.cov = prm;
       x.flops = 0.0;
       x.evals = 0;
@@ -295,6 +299,16 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<R>::value) tt_cross_kernel
       r.max_rank = maxrank;
       r.fail_step = status == ST_INVALID ? 5 : x.fail_step;
       results[jid] = r;
+    }
+    if (piv_out && tid < 32) {  // the final right sets (latest right-to-left half-sweep)
+      uint16_t* rec = piv_out + (size_t)jid * pstride;
+      int off = 0;
+      for (int k = 1; k < d; ++k) {
+        const int c = x.rsz[k], w = d - k;
+        if (tid == 0) rec[off] = (uint16_t)c;
+        for (int idx = tid; idx < c * w; idx += 32) rec[off + 1 + idx] = rset_at(x, k, idx / w)[idx % w];
+        off += 1 + c * w;
+      }
     }
     __syncthreads();
   }
@@ -504,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 2) bracket_kernel(const JobDesc* __r
   cpx<R>* Gf = reinterpret_cast<cpx<R>*>(smem + S.Gf);
   double* redv = reinterpret_cast<double*>(smem + S.red);
   int* redi = reinterpret_cast<int*>(redv + 2);
-  constexpr int kAcc = 4;  // accumulator entries per thread: rank <= 32 on both trains
+  constexpr int kAcc = 4;  // accumulator entries per thread: r_v r_phi <= 1024 (the host checks)
   for (;;) {  // brackets from a queue: a CTA that shares its SM takes fewer
     __syncthreads();  // every thread has read the previous slot
     if (tid == 0) slot = atomicAdd(counter, 1);
@@ -659,6 +673,9 @@ __global__ void __launch_bounds__(kThreads, 2) bracket_kernel(const JobDesc* __r
               }
             }
           }
+          // a train above rank 32 (r_{k-1} r_k > kAcc kThreads): the rest evaluated directly
+          for (int idx = tid + kAcc * kThreads; idx < rp * rk; idx += kThreads)
+            A[idx] = eval_point(x, idx / rk, i, idx % rk);
         }
         __syncthreads();
         // X = E A^phi(i): rpv x rkf
@@ -783,8 +800,9 @@ bool resolve(const tt_options* in, Resolved* r) {
   if (o.engine < TT_ENGINE_AUTO || o.engine > TT_ENGINE_TENSOR_CORES) return false;
   if (o.graph != 0 && o.graph != 1) return false;
   if (o.method != TT_METHOD_SINGLE_TRAIN && o.method != TT_METHOD_TWO_TRAINS) return false;
+  if (o.pivot_io != 0 && o.pivot_io != 1) return false;
   const bool two = o.method == TT_METHOD_TWO_TRAINS;
-  if (two && (o.max_rank > 32 || o.max_n > 1024)) return false;  // the bracket kernel's tile sizes
+  if (two && (o.max_rank > 40 || o.max_n > 1024)) return false;  // the bracket kernel's tile sizes
   if (o.precision == TT_FP64) {
     if (o.engine == TT_ENGINE_TENSOR_CORES) return false;  // no FP64 tensor-core product
     o.engine = TT_ENGINE_CUDA_CORES;
@@ -847,6 +865,7 @@ Layout make_layout(const tt_options& o, bool f64) {
   L.P = take(2 * r * r * 2 * rs);  // P and the copy maxvol falls back to
   L.sacc = take(r * r * 16);
   L.chain = take(2 * r * 16);
+  L.cb = take(sizeof(float) * ttp::kBoundCap);
   L.stride = align_up(off, A);
   L.dmax = (int)d;
   L.nmax = (int)n;
@@ -920,13 +939,14 @@ ttp::BrSmem make_brsmem(const tt_options& o, bool f64) {
     S.rsz[f] = take((d + 1) * 4);
     S.W[f] = take(r * 4);
   }
-  S.E = take(r * r * cs);
+  const int rr = std::min(r * r, 1024);  // E and its products: r_v r_phi <= 1024
+  S.E = take(rr * cs);
   // X .. Gf are contiguous: the FP64 Gauss-Jordan buffer [P | I] (r x 2r) aliases them
-  S.X = take(r * r * cs);
+  S.X = take(rr * cs);
   S.Av = take(r * r * cs);
   S.Af = take(r * r * cs);
-  S.Gv = take(r * r * cs);
-  S.Gf = take(std::max(r * r * cs, 2 * r * r * 16 - (off - S.X)));
+  S.Gv = take(rr * cs);
+  S.Gf = take(std::max(rr * cs, 2 * r * r * 16 - (off - S.X)));
   S.Mv = take(r * r * cs);
   S.Mf = take(r * r * cs);
   S.red = take(32);
@@ -939,6 +959,8 @@ struct DevLayout {  // offsets inside the device workspace
   size_t o_jobs, o_params, o_order, o_first, o_count, o_hstatus, o_pairs;  // inside the stage block
   size_t o_host;  // host-only scratch of the preparation (never copied to the device)
   size_t o_disc;  // host-only: per-problem relative discretisation-error factor
+  size_t o_warm;  // warm-start records, pstride entries per job (pivot_io)
+  size_t pivots, pstride;  // device: final right sets, pstride entries per job (pivot_io)
 };
 
 // doubles of host scratch the preparation of one problem needs (d <= max_d):
@@ -964,6 +986,8 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   D.o_pairs = take(two ? sizeof(int2) * (size_t)R.max_jobs / 2 : 0);
   D.o_host = take(sizeof(double) * host_scratch_doubles((size_t)R.o.max_d));
   D.o_disc = take(sizeof(double) * R.o.max_batch);
+  D.pstride = ttp::pivot_record_entries(R.o.max_d, R.o.max_rank);
+  D.o_warm = take(R.o.pivot_io ? sizeof(uint16_t) * D.pstride * (size_t)R.max_jobs : 0);
   D.stage_bytes = s;
   size_t off = 0;
   auto take2 = [&](size_t bytes) {
@@ -979,6 +1003,7 @@ DevLayout make_dev_layout(const Resolved& R, const Layout& L, int grid) {
   // two-train form: every factor train's skeleton records, one per core
   D.emit_stride = two ? align_up(ttp::emit_core_bytes(L.rmax, L.dmax) * L.dmax, A) : 0;
   D.emit = take2(D.emit_stride * (two ? (size_t)R.max_jobs : 0));
+  D.pivots = take2(R.o.pivot_io ? sizeof(uint16_t) * D.pstride * (size_t)R.max_jobs : 0);
   D.total = off;
   return D;
 }
@@ -1109,7 +1134,7 @@ struct tt_pricer {
   char* h_pack;            // pinned, packed copy that is sent to the device
   InstanceResult* h_ires;  // pinned
   int count, njobs, npairs;
-  size_t p_jobs, p_params, p_order, p_first, p_count, p_hstatus, p_pairs, p_bytes;  // packed offsets
+  size_t p_jobs, p_params, p_order, p_first, p_count, p_hstatus, p_pairs, p_warm, p_bytes;  // packed offsets
   ttp::BrSmem bsm;  // two-train form: the bracket kernel's shared-memory carve
   int bgrid;
   size_t last_h2d, last_d2h;
@@ -1125,8 +1150,33 @@ namespace {
 
 // Validation of one problem (FP64, host); `scr` holds d*d doubles.  Returns
 // TT_OK or the problem's status.
+// Entries of a warm-start record for d assets and `terms` trains, or -1 when it
+// is malformed: counts above the rank cap, indices outside the grid, repeated
+// multi-indices within a bond.
+long long warm_record_entries(const unsigned short* w, int d, int terms, int rank, int n) {
+  long long off = 0;
+  for (int t = 0; t < terms; ++t)
+    for (int k = 1; k < d; ++k) {
+      const int c = w[off], wd = d - k;
+      if (c > rank) return -1;
+      const unsigned short* e = w + off + 1;
+      for (int i = 0; i < c * wd; ++i)
+        if (e[i] >= n) return -1;
+      for (int a = 0; a < c; ++a)
+        for (int b = 0; b < a; ++b)
+          if (std::memcmp(e + a * wd, e + b * wd, sizeof(unsigned short) * wd) == 0) return -1;
+      off += 1 + (long long)c * wd;
+    }
+  return off;
+}
+
 int validate_problem(const tt_problem& p, const tt_options& o, double* scr) {
   const int d = p.d;
+  if (o.method == TT_METHOD_TWO_TRAINS) {  // the phi train's bond dimension, and the bracket's E
+    const int rphi = p.max_rank_phi > 0 ? p.max_rank_phi : p.max_rank;
+    if (p.max_rank_phi < 0) return TT_ERR_INVALID;
+    if (rphi > o.max_rank || (long long)p.max_rank * rphi > 1024) return TT_ERR_CAPACITY;
+  }
   if (d < 1 || d > o.max_d || p.n_grid < 2 || p.n_grid > o.max_n || p.max_rank < 1 || p.max_rank > o.max_rank ||
       !p.spot || !p.cov || !p.damping || (p.payoff != TT_MIN_CALL && p.payoff != TT_MAX_CALL))
     return (d > o.max_d || p.n_grid > o.max_n || p.max_rank > o.max_rank) ? TT_ERR_CAPACITY : TT_ERR_INVALID;
@@ -1137,6 +1187,11 @@ int validate_problem(const tt_problem& p, const tt_options& o, double* scr) {
   for (int j = 0; j < d; ++j)
     if (!(p.spot[j] > 0)) return TT_ERR_INVALID;
   if (!cholesky_ok(p.cov, d, scr)) return TT_ERR_NOT_PD;
+  if (p.warm_sets) {  // warm starts: single-train form with pivot_io, a well-formed record
+    if (!o.pivot_io || o.method != TT_METHOD_SINGLE_TRAIN) return TT_ERR_INVALID;
+    if (warm_record_entries(p.warm_sets, d, p.payoff == TT_MIN_CALL ? 1 : d, p.max_rank, p.n_grid) < 0)
+      return TT_ERR_INVALID;
+  }
   if (p.payoff == TT_MIN_CALL) {
     double sd = 0.0;
     int stv = TT_OK;
@@ -1270,6 +1325,7 @@ void derive_trains(const Resolved& R, const tt_problem& p, int i, bool two, JobD
         const bool vh = fi == 0;
         JobDesc jd = base_job(term);
         jd.factor = vh ? ttp::FACTOR_VHAT : ttp::FACTOR_PHI;
+        if (!vh && p.max_rank_phi > 0) jd.rmax = p.max_rank_phi;  // D_phi
         jd.Tq = vh ? 0.0 : T;
         double* cv = params + poff;
         double* dl = cv + (size_t)d * d;
@@ -1383,6 +1439,8 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   int2* pairs = reinterpret_cast<int2*>(st + h->dl.o_pairs);
   double* scr = reinterpret_cast<double*>(st + h->dl.o_host);
   double* disc = reinterpret_cast<double*>(st + h->dl.o_disc);
+  uint16_t* warm = reinterpret_cast<uint16_t*>(st + h->dl.o_warm);
+  size_t wused = 0;
   const bool two = o.method == TT_METHOD_TWO_TRAINS;
   int nj = 0, np = 0;
   size_t poff = 0;
@@ -1392,8 +1450,21 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
     hstat[i] = validate_problem(probs[i], o, scr);
     disc[i] = std::nan("");
     if (hstat[i] == TT_OK) {
+      const int j0 = nj;
       derive_trains(h->R, probs[i], i, two, jobs, params, pairs, nj, np, poff, cnt, scr);
       disc[i] = disc_factor(probs[i]);
+      for (int j = j0; j < nj; ++j) jobs[j].warm_off = -1;
+      if (probs[i].warm_sets) {  // validated: one record per train, each job its own copy
+        const tt_problem& p = probs[i];
+        const unsigned short* w = p.warm_sets;
+        for (int j = j0; j < nj; ++j) {
+          const long long len = warm_record_entries(w, p.d, 1, p.max_rank, p.n_grid);
+          std::memcpy(warm + (size_t)wused, w, sizeof(uint16_t) * len);
+          jobs[j].warm_off = (int)wused;
+          wused += len;
+          w += len;
+        }
+      }
     }
   }
   // largest jobs first, ties by job number (std::sort works in place)
@@ -1420,6 +1491,7 @@ int prepare_impl(tt_pricer* h, const tt_problem* probs, int count) {
   h->p_count = put(h->dl.o_count, sizeof(int) * count);
   h->p_hstatus = put(h->dl.o_hstatus, sizeof(int) * count);
   h->p_pairs = put(h->dl.o_pairs, sizeof(int2) * np);
+  h->p_warm = put(h->dl.o_warm, sizeof(uint16_t) * wused);
   h->p_bytes = off;
   h->last_h2d = off;
   if (off && cudaMemcpyAsync(h->ws + h->dl.stage, h->h_pack, off, cudaMemcpyHostToDevice,
@@ -1443,17 +1515,23 @@ int launch_all(tt_pricer* h, cudaStream_t stream) {
   if (cudaMemsetAsync(counter, 0, 2 * sizeof(int), stream) != cudaSuccess) return TT_ERR_CUDA;
   char* emit = h->ws + h->dl.emit;
   const size_t es = h->dl.emit_stride;
+  // pivot records (tt_options.pivot_io): warm starts in, final right sets out
+  const uint16_t* warm = h->R.o.pivot_io ? reinterpret_cast<const uint16_t*>(st + h->p_warm) : nullptr;
+  uint16_t* pout = h->R.o.pivot_io ? reinterpret_cast<uint16_t*>(h->ws + h->dl.pivots) : nullptr;
   if (h->njobs > 0) {
     const int grid = std::min(h->grid, h->njobs);
     if (h->R.o.precision == TT_FP64)
       ttp::tt_cross_kernel<double, false><<<grid, ttp::kThreads, h->sml.total, stream>>>(
-          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es);
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es, warm, pout,
+          (int)h->dl.pstride);
     else if (h->R.o.engine == TT_ENGINE_TENSOR_CORES)
       ttp::tt_cross_kernel<float, true><<<grid, ttp::kThreads, h->sml.total, stream>>>(
-          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es);
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es, warm, pout,
+          (int)h->dl.pstride);
     else
       ttp::tt_cross_kernel<float, false><<<grid, ttp::kThreads, h->sml.total, stream>>>(
-          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es);
+          jobs, params, order, h->njobs, counter, jres, scratch, h->lay, h->sml, h->R.kn, emit, es, warm, pout,
+          (int)h->dl.pstride);
     if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
   }
   if (h->npairs > 0) {  // two-train form: the brackets, two scratch blocks per CTA
@@ -1639,7 +1717,8 @@ int tt_price_create(const tt_options* opt, tt_pricer** out) {
   h->h_stage = nullptr;
   h->h_pack = nullptr;
   h->h_ires = nullptr;
-  h->p_jobs = h->p_params = h->p_order = h->p_first = h->p_count = h->p_hstatus = h->p_pairs = h->p_bytes = 0;
+  h->p_jobs = h->p_params = h->p_order = h->p_first = h->p_count = h->p_hstatus = h->p_pairs = h->p_warm =
+      h->p_bytes = 0;
   h->last_h2d = h->last_d2h = 0;
   h->cap = nullptr;
   h->ev_in = h->ev_out = nullptr;
@@ -1714,6 +1793,42 @@ int tt_price_transfer_bytes(const tt_pricer* h, size_t* h2d, size_t* d2h) {
   if (h2d) *h2d = h->last_h2d;
   if (d2h) *d2h = h->last_d2h;
   return TT_OK;
+}
+
+size_t tt_pivot_record_entries(int max_d, int max_rank) {
+  if (max_d < 1 || max_rank < 1) return 0;
+  return ttp::pivot_record_entries(max_d, max_rank);
+}
+
+int tt_price_pivots(tt_pricer* h, int problem, unsigned short* out, size_t cap) {
+  if (!h || !out || problem < 0 || problem >= h->count) return TT_ERR_INVALID;
+  if (!h->R.o.pivot_io) return TT_ERR_INVALID;
+  if (cudaSetDevice(h->R.o.device) != cudaSuccess) return TT_ERR_CUDA;
+  const char* st = h->h_stage;
+  const int first = reinterpret_cast<const int*>(st + h->dl.o_first)[problem];
+  const int cnt = reinterpret_cast<const int*>(st + h->dl.o_count)[problem];
+  const JobDesc* jobs = reinterpret_cast<const JobDesc*>(st + h->dl.o_jobs);
+  size_t used = 0;
+  for (int j = first; j < first + cnt; ++j) {
+    // the record's length follows from its counts; fetch the whole stride
+    const size_t stride = h->dl.pstride;
+    if (used + stride > cap && used + 1 > cap) return TT_ERR_CAPACITY;
+    uint16_t* dst = reinterpret_cast<uint16_t*>(out + used);
+    const size_t n = std::min(stride, cap - used);
+    if (cudaMemcpyAsync(dst, h->ws + h->dl.pivots + sizeof(uint16_t) * stride * (size_t)j, sizeof(uint16_t) * n,
+                        cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return TT_ERR_CUDA;
+    size_t len = 0;
+    const int d = jobs[j].d;
+    for (int k = 1; k < d; ++k) {
+      if (len >= n) return TT_ERR_CAPACITY;
+      len += 1 + (size_t)dst[len] * (d - k);
+    }
+    if (len > n) return TT_ERR_CAPACITY;
+    used += len;
+  }
+  return (int)used;
 }
 
 const char* tt_status_string(int status) {
@@ -1838,6 +1953,7 @@ extern "C" int tt_price_evaluate_static(const tt_problem* probs, int count, int 
   h.njobs = 0;
   h.npairs = 0;
   h.p_pairs = 0;
+  h.p_warm = 0;
   h.last_h2d = h.last_d2h = 0;
   rc = prepare_impl(&h, probs, count);
   if (rc != TT_OK) return rc;

@@ -8,7 +8,7 @@
 
 namespace ttp {
 
-enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3, MISC_SING = 4, MISC_MBAR = 8,
+enum : int { MISC_JOB = 0, MISC_PIV = 1, MISC_FAIL = 2, MISC_DRAW = 3, MISC_SING = 4, MISC_OLDW = 5, MISC_MBAR = 8,
              MISC_TMEM = 12 };  // MISC_MBAR: two 8-byte barriers (ints 8..11)
 
 // Functions templated on <R, bool TC>: TC selects the maxvol block-product engine,
@@ -158,14 +158,27 @@ __device__ void job_setup(Ctx<R>& x, const JobDesc& jd, const double* prm, doubl
         }
         return (uint16_t)(splitmix64(pivot_key(jd.seed, jd.term, k, t, bb, j)) % n);
       };
-      uint16_t* c0 = rset_at(x, k, 0);
-      for (int pos = lane; pos < width; pos += 32) c0[pos] = (uint16_t)(n / 2);
-      for (int bb = 1 + lane; bb < rk; bb += 32) {
+      // a warm start fills the first slots from its record; otherwise slot 0 is
+      // the grid centre; the remaining slots are drawn
+      int first = 0;
+      if (x.warm) {
+        const uint16_t* w = x.warm;
+        for (int kk = 1; kk < k; ++kk) w += 1 + (int)w[0] * (d - kk);  // this bond's part
+        first = min((int)w[0], (int)rk);
+        for (int idx = lane; idx < first * width; idx += 32)
+          rset_at(x, k, idx / width)[idx % width] = w[1 + idx];
+      }
+      if (first == 0) {
+        uint16_t* c0 = rset_at(x, k, 0);
+        for (int pos = lane; pos < width; pos += 32) c0[pos] = (uint16_t)(n / 2);
+        first = 1;
+      }
+      for (int bb = first + lane; bb < rk; bb += 32) {
         uint16_t* dst = rset_at(x, k, bb);
         for (int pos = 0; pos < width; ++pos) dst[pos] = coord(bb, 0, pos);
       }
       __syncwarp();
-      for (int bb = 1; bb < rk; ++bb) {
+      for (int bb = first; bb < rk; ++bb) {
         uint16_t* dst = rset_at(x, k, bb);
         bool fresh = false;
         for (int t = 0; t < 65536 && !fresh; ++t) {
@@ -851,6 +864,71 @@ __device__ int rank_reveal(Ctx<R>& x, int rho, R thr2) {
 // ---------------------------------------------------------------------------
 constexpr int kRefreshSwaps = 16;
 
+// ---------------------------------------------------------------------------
+// Skipping provably swap-free revisits (bound_prepare / bound_apply at each
+// swap, bound_store after each visit).  After a visit of block q, cb[q][t]
+// holds the largest |B_rt| of the block's non-pivot rows.  A swap of row i into
+// slot j updates every row by B'_r = B_r - B_rj (B_i - e_j) / B_ij, so
+// |B'_rt| <= |B_rt| + |B_rj| v_t with v_t = |B_it - [t = j]| / |B_ij|, and the
+// bounds of the other blocks follow as cb[q][t] += cb[q][j] v_t; the pivot row
+// the swap releases (B = e_j before) gets at most [t = j] + v_t.  A revisit of a
+// block whose bounds are all within 1 + tau finds no entry to swap, so it is
+// skipped: the rows and the prices are those of the full revisit.
+// ---------------------------------------------------------------------------
+// block-uniform: true when block beta's bounds allow no swap
+__device__ __forceinline__ bool bound_allows_skip(const float* cb, int beta, int rho, float lim) {
+  bool over = false;
+  for (int t = threadIdx.x; t < rho; t += kThreads) over |= !(cb[beta * rho + t] <= lim);
+  return !__syncthreads_or(over);
+}
+
+// after a visit: block beta's column maxima over its non-pivot rows (B column-major,
+// leading dimension b); rounding slack keeps the bound above the stored values
+template <typename R>
+__device__ void bound_store(float* cb, int beta, const cpx<R>* B, int b, int bs, int rho,
+                            const unsigned char* inw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = warp; t < rho; t += kWarps) {
+    R mx = R(0);
+    for (int r = lane; r < bs; r += 32)
+      if (!inw[r]) mx = fmax(mx, cabs2(B[t * b + r]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) cb[beta * rho + t] = (mx == mx) ? sqrtf((float)mx) * 1.0001f : INFINITY;
+  }
+}
+
+// A swap of row i into slot j of block beta, in two phases around the swap's
+// barrier.  Before it: v_t from B's row i (still unchanged) and a snapshot of
+// every block's column-j bound, after the bounds (kept in the bound buffer past
+// the nb x rho bounds).  After it: every bound of every other block, one FMA
+// each; the block of the pivot row the swap releases (`oldb`) also takes
+// [t = j] + v_t.
+template <typename R>
+__device__ void bound_prepare(float* cb, int nb, int rho, int j, const cpx<R>* B, int b, int i) {
+  float* cj = cb + nb * rho;
+  float* v = cj + nb;
+  const float piv = sqrtf((float)cabs2(B[j * b + i]));
+  for (int t = threadIdx.x; t < rho; t += kThreads) {
+    cpx<R> e = B[t * b + i];
+    if (t == j) e.re -= R(1);
+    v[t] = sqrtf((float)cabs2(e)) / piv;
+  }
+  for (int q = threadIdx.x; q < nb; q += kThreads) cj[q] = cb[q * rho + j];
+}
+
+__device__ __forceinline__ void bound_apply(float* cb, int nb, int rho, int beta, int j, int oldb) {
+  const float* cj = cb + nb * rho;
+  const float* v = cj + nb;
+  for (int idx = threadIdx.x; idx < nb * rho; idx += kThreads) {
+    const int q = idx / rho, t = idx - q * rho;
+    if (q == beta) continue;
+    float nv = fmaf(cj[q], v[t], cb[idx]);
+    if (q == oldb) nv = fmaxf(nv, (t == j ? 1.0f : 0.0f) + v[t]);
+    cb[idx] = nv == nv ? nv : INFINITY;
+  }
+}
+
 template <typename R>
 __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
   const int tid = threadIdx.x, N = x.n;
@@ -869,6 +947,12 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
   for (int t = 0; t < rho; ++t) ncs = max(ncs, x.jp[t] + 1);
   cpx<R>* Psave = x.P + x.rall * x.rall;
   bool saved = false, frozen = false;
+  // revisit bounds (see bound_prepare); blocks not yet visited have none
+  const bool cbon = nb * (rho + 1) + rho <= kBoundCap;  // bounds, column-j snapshot, v
+  const float blim = sqrtf((float)thr);
+  if (cbon)
+    for (int idx = tid; idx < nb * rho; idx += kThreads) x.cb[idx] = INFINITY;
+  int skipped = 0;
   while (quiet < nb && visits < 4 * nb) {
     if (since_inv >= kRefreshSwaps && !frozen) {
       TTP_TIC(t_inv);
@@ -901,6 +985,13 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       TTP_TOC(t_inv, 5);
     }
     if (frozen && visits >= nb) break;
+    if (cbon && !frozen && visits >= nb && bound_allows_skip(x.cb, beta, rho, blim)) {
+      ++quiet;  // a swap-free revisit, known without the block product
+      ++visits;
+      ++skipped;
+      beta = (beta + 1) % nb;
+      continue;
+    }
     TTP_TIC(t_rev);
     const int rs = beta * b;
     const int bs = min(b, m - rs);
@@ -1015,12 +1106,15 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       }
       if (tid == 0) {
         const int old = x.wrow[j] - rs;
+        x.misc[MISC_OLDW] = x.wrow[j];
         if (old >= 0 && old < bs) inw[old] = 0;
         inw[i] = 1;
         x.wrow[j] = rs + i;
       }
+      if (cbon) bound_prepare(x.cb, nb, rho, j, A, b, i);
       __syncthreads();
       eval_prow(x, j, rs + i, rho);
+      if (cbon) bound_apply(x.cb, nb, rho, beta, j, x.misc[MISC_OLDW] / b);
       const cpx<R> ipiv = crecip(x.swrow[j]);
       bv = R(-1);
       bi = INT_MAX;
@@ -1046,6 +1140,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       ++since_inv;
       ++nswaps;
     }
+    if (cbon && !frozen) bound_store(x.cb, beta, A, b, bs, rho, inw);
     quiet = swapped ? 0 : quiet + 1;
     ++visits;
     beta = (beta + 1) % nb;
@@ -1054,7 +1149,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
   }
   if (tid == 0) {
     x.swaps += nswaps;
-    x.visits += visits;
+    x.visits += visits - skipped;  // block products made
   }
 }
 
@@ -1110,6 +1205,12 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
   for (int t = 0; t < rho; ++t) ncs = max(ncs, x.jp[t] + 1);
   cpx<R>* Psave = x.P + x.rall * x.rall;
   bool saved = false, frozen = false;
+  // revisit bounds (see bound_prepare); blocks not yet visited have none
+  const bool cbon = nb * (rho + 1) + rho <= kBoundCap;  // bounds, column-j snapshot, v
+  const float blim = sqrtf((float)thr);
+  if (cbon)
+    for (int idx = tid; idx < nb * rho; idx += kThreads) x.cb[idx] = INFINITY;
+  int skipped = 0;
   while (quiet < nb && visits < 4 * nb) {
     if (since_inv >= kRefreshSwaps && !frozen) {
       TTP_TIC(t_inv);
@@ -1142,6 +1243,13 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       TTP_TOC(t_inv, 5);
     }
     if (frozen && visits >= nb) break;
+    if (cbon && !frozen && visits >= nb && bound_allows_skip(x.cb, beta, rho, blim)) {
+      ++quiet;  // a swap-free revisit, known without the block product
+      ++visits;
+      ++skipped;
+      beta = (beta + 1) % nb;
+      continue;
+    }
     TTP_TIC(t_rev);
     const int rs = beta * b;
     const int bs = min(b, m - rs);
@@ -1167,7 +1275,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       bool ok = true;
       if (!frozen && c >= kTcBufs) {  // the products that last read this buffer (checked at the next barrier)
         const int pk = (c - kTcBufs) & 1;
-        ok = tc::mbar_wait(x.mbar + pk, phase[pk]);
+        ok = tc::mbar_wait(x.mbar + pk, phase[pk], tc::kLoopWaitLimit);
         if (ok) phase[pk] ^= 1u;  // a phase that timed out stays the outstanding one
       }
       // evaluation: lane -> rows 8g + lane/4 (two row groups per warp), columns
@@ -1266,7 +1374,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       bool ok = true;
       for (int c = max(0, nch - kTcBufs); c < nch; ++c) {
         const int bufk = c & 1;
-        const bool done = tc::mbar_wait(x.mbar + bufk, phase[bufk]);
+        const bool done = tc::mbar_wait(x.mbar + bufk, phase[bufk], tc::kLoopWaitLimit);
         if (done) phase[bufk] ^= 1u;
         ok = ok && done;
       }
@@ -1329,12 +1437,15 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       }
       if (tid == 0) {
         const int old = x.wrow[j] - rs;
+        x.misc[MISC_OLDW] = x.wrow[j];
         if (old >= 0 && old < bs) inw[old] = 0;
         inw[i] = 1;
         x.wrow[j] = rs + i;
       }
+      if (cbon) bound_prepare(x.cb, nb, rho, j, B, b, i);
       __syncthreads();
       eval_prow(x, j, rs + i, rho);  // P[j][t] = A(i, t), FP32
+      if (cbon) bound_apply(x.cb, nb, rho, beta, j, x.misc[MISC_OLDW] / b);
       const cpx<R> ipiv = crecip(x.swrow[j]);
       bv = R(-1);
       bi = INT_MAX;
@@ -1362,6 +1473,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       ++since_inv;
       ++nswaps;
     }
+    if (cbon && !frozen) bound_store(x.cb, beta, B, b, bs, rho, inw);
     quiet = swapped ? 0 : quiet + 1;
     ++visits;
     beta = (beta + 1) % nb;
@@ -1370,7 +1482,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
   }
   if (tid == 0) {
     x.swaps += nswaps;
-    x.visits += visits;
+    x.visits += visits - skipped;  // block products made
     if (!x.tc_pending) x.mma_phase = phase[0] | (phase[1] << 1);
   }
   __syncthreads();

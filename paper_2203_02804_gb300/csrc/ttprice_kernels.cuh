@@ -145,8 +145,14 @@ struct JobDesc {
   double cap;  // no-arbitrage bound on the train's share of the price: the sum of the spots
   double theta;    // rank threshold of this job (its class's, else the options')
   int block_rows;  // rows per elimination/maxvol block of this job
-  int pad_;
+  int warm_off;    // offset of this job's warm-start record in the warm buffer (-1: none)
 };
+
+// Pivot records (warm starts and the final right sets): for k = 1..d-1 a count
+// c_k, then c_k multi-indices over axes k..d-1.  Entries of the largest record.
+__host__ __device__ inline size_t pivot_record_entries(int dmax, int rmax) {
+  return (size_t)(dmax > 0 ? dmax - 1 : 0) + (size_t)rmax * dmax * (dmax > 0 ? dmax - 1 : 0) / 2;
+}
 
 // Skeleton of a factor train's core k (two-train form), written by the cross at
 // each left-to-right core: rank rho, the selected fiber rows W[t] = o N + i (o
@@ -180,9 +186,13 @@ struct Knobs {
 
 // per-CTA global scratch, byte offsets (pair: PairE<R> entries)
 struct Layout {
-  size_t u, lam, om, lset, rset, lstate, rstate, lvec, rvec, pair, P, sacc, chain, stride;
+  size_t u, lam, om, lset, rset, lstate, rstate, lvec, rvec, pair, P, sacc, chain, cb, stride;
   int dmax, nmax, rmax;
 };
+
+// maxvol's per-block, per-column bounds on |B| (floats per CTA): a core whose
+// blocks x rank exceed it revisits every block
+constexpr int kBoundCap = 8192;
 
 // shared-memory carve, byte offsets (sizes depend on R)
 struct SmemLayout {
@@ -302,6 +312,7 @@ struct Ctx {
   double2* sacc;      // [rmax_all][rmax_all]
   double2* vchain;    // [rmax_all]
   double2* ychain;    // [rmax_all]
+  float* cb;          // [kBoundCap] maxvol revisit bounds
   int dmax, nmax, rall;
   // shared
   cpx<R>* sw;
@@ -342,6 +353,7 @@ struct Ctx {
   int tc_pending;  // a completion wait gave up: wait again before releasing TMEM
   int fail_step;
   char* emit;      // two-train form: this job's skeleton records (NULL: none)
+  const uint16_t* warm;  // this job's warm-start record (NULL: draw every initial pivot)
 };
 
 // Index sets: left set at bond k holds multi-indices over axes 0..k-1,

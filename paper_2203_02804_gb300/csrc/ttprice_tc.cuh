@@ -16,6 +16,14 @@ namespace tc {
 
 constexpr int kRows = 128;  // MMA M: maxvol block rows (block_rows <= 128, padded with zeros)
 constexpr uint32_t kWaitLimit = 1u << 24;  // bounded spin on the completion barrier
+// The waits inside maxvol's visit loop may be shortened at build time (a test
+// build makes them give up at once, to exercise the failure path); the wait
+// before the accumulators are released keeps kWaitLimit, so no product is in
+// flight when the tensor memory is freed.
+#ifndef TTP_TC_LOOP_WAIT
+#define TTP_TC_LOOP_WAIT (1u << 24)
+#endif
+constexpr uint32_t kLoopWaitLimit = TTP_TC_LOOP_WAIT;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -65,10 +73,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t arrivals) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// wait for completion of phase `parity`; false after kWaitLimit polls
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// wait for completion of phase `parity`; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = kWaitLimit) {
   const uint32_t a = smem_u32(mbar);
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"

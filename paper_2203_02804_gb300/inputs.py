@@ -30,6 +30,8 @@ class Problem:
     max_rank: int
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    max_rank_phi: int = 0       # two-train form: D_phi (0: max_rank, which is D_v)
+    warm_sets: object = None    # warm-start record (uint16 array, include/ttprice.h format) or None
 
     @property
     def d(self) -> int:
@@ -169,16 +171,41 @@ def random_correlation(d, rng):
     return a * np.outer(s, s)
 
 
-def high_dim_problem(d, payoff="min", n_grid=256, trunc_L=40.0, max_rank=64, index=3):
+def balanced_truncation(n_grid, rate_axis, d, s2t):
+    """L balancing the midpoint rule's two errors on a d-axis grid of N points:
+    aliasing, about d exp(-pi a N / L) for damping rate a per axis, and the cut
+    Gaussian tail exp(-s^2 T L^2 / 2) of the slowest axis (solved by bisection)."""
+    lo, hi = 1e-3, 1e4
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        f = np.pi * rate_axis * n_grid / mid - np.log(d) - 0.5 * s2t * mid * mid
+        lo, hi = (mid, hi) if f > 0 else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+def high_dim_problem(d, payoff="min", n_grid=256, trunc_L=None, max_rank=64, index=3, damping=None):
     """d in {20, 50, 100}: sigma_j~U[0.15,0.35], random correlation as above,
-    K=100, S0=100, r=0.02, T=1, damping alpha_j = -5/d (the paper's own high-d
-    choice, Section V).  A fixed alpha_j = -1.5 makes the integrand's scale
-    e^{T delta' Cov delta / 2} reach ~e^90 at d = 50, far past any precision."""
+    K=100, S0=100, r=0.02, T=1.
+
+    Damping: for the call on the maximum, |alpha_j| = 10/d.  Term j's integrand
+    carries exp(T/2 (1 + d|alpha|)^2 sigma_j^2 + ...) through the maximum's axis, so
+    a fixed |alpha| makes its scale e^{T delta' Cov delta / 2} reach ~e^180 at d = 50
+    (alpha = -1.5), and FP32 sums lose everything to cancellation; at 10/d the
+    coefficient stays 11.  The call on the minimum keeps alpha_j = -1.5 (its scale
+    grows only like alpha^2 sigma^2 d).  L balances aliasing at the damping rate
+    against the cut tail of the slowest axis (``balanced_truncation``), unless
+    given: with N = 256 that predicts ~5e-5 of discretisation error at d = 20,
+    ~1e-2 at d = 50 and ~2e-1 at d = 100 for the call on the maximum."""
     rng = np.random.default_rng(SEED_BASE + index * 1000 + d)
     sigma = rng.uniform(0.15, 0.35, d)
     corr = random_correlation(d, rng)
+    if damping is None:
+        damping = -10.0 / d if payoff == "max" else -1.5
+    if trunc_L is None:
+        rate = abs(damping)
+        trunc_L = float(balanced_truncation(n_grid, rate, d, float(sigma.min()) ** 2))
     return Problem(spot=np.full(d, 100.0), cov=cov_from(sigma, corr), rate=0.02, maturity=1.0,
-                   strike=100.0, payoff=payoff, damping=np.full(d, -5.0 / d), n_grid=n_grid,
+                   strike=100.0, payoff=payoff, damping=np.full(d, float(damping)), n_grid=n_grid,
                    trunc_L=trunc_L, max_rank=max_rank, seed=SEED_BASE + index * 1000 + d,
                    meta={"workload": f"d{d}-{payoff}-call"})
 

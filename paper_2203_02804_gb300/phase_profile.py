@@ -1,6 +1,6 @@
 """Where a CTA's time goes: per-phase clock64() totals of the TT-cross kernel.
 
-    python -m paper_2203_02804_gb300.phase_profile [--batch 1216] [--precision mixed]
+    python -m paper_2203_02804_gb300.phase_profile [--batch 1216] [--precision mixed] [--engine cuda] [--rank-tol 1e-5]
 
 Builds a profiling variant of the library (-DTTP_PHASE_TIMERS; thread 0 of each
 CTA adds the clock span of each phase, barrier waits included) into a temporary
@@ -32,6 +32,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--batch", type=int, default=1216)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--engine", choices=["auto", "cuda", "tc"], default="auto")
+    ap.add_argument("--rank-tol", type=float, default=0.0, help="0: the library default")
     args = ap.parse_args()
     import torch
 
@@ -44,7 +46,8 @@ def main():
     L = ttprice._lib
     L.tt_phase_cycles.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
     ps = inputs.five_asset_batch(args.batch)
-    pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=args.batch, precision=args.precision)
+    pr = ttprice.Pricer(max_d=5, max_n=128, max_rank=32, max_batch=args.batch, precision=args.precision,
+                        engine=args.engine, rank_tol=args.rank_tol)
     pr.prepare(ps)
     pr.run()
     torch.cuda.synchronize()
@@ -59,6 +62,7 @@ def main():
     nested = {i for i, name in enumerate(PHASES) if name.startswith("  (in ")}
     tot = sum(v for i, v in enumerate(buf) if i not in nested)
     print(json.dumps({"workload": "d5-min-call N=128 rank 32", "precision": args.precision,
+                      "engine": args.engine, "rank_tol": args.rank_tol or "default",
                       "batch": args.batch, "prices_per_s": args.batch / dt}))
     for i, name in enumerate(PHASES):
         if buf[i]:

@@ -10,7 +10,8 @@ point for TT-cross at high dimension as open, Section VI).
 Network: 15 -> 256 -> 256 -> 256 -> 256 -> 1, SiLU on the hidden layers,
 FP32 master weights trained by the library's kernels (include/ttmlp.h:
 tiled GEMMs, fused activation, Adam); bfloat16 copies of the weights for
-inference (products still accumulate in FP32).
+inference, whose 256-wide layers run on the tensor cores (tcgen05.mma
+kind::f16, bfloat16 activations, FP32 accumulation in tensor memory).
 
 Features (15): S0_j / K (5), sigma_j = sqrt(Cov_jj) (5), the mean off-diagonal
 correlation, K / 100, T, r, and the mean damping -alpha.  Targets are
@@ -42,7 +43,8 @@ def _bind(lib):
     lib.tt_mlp_to_bf16.argtypes = [_P, _P, _LL, _P]
     lib.tt_mlp_ensemble.argtypes = [_P, _I, _I, _P, _P, _P]
     lib.tt_mlp_gather.argtypes = [_P, _P, _I, _I, _P, _P]
-    for f in ("forward", "forward_bf16", "backward", "mse", "adam", "to_bf16", "ensemble", "gather"):
+    lib.tt_mlp_forward_tc.argtypes = [_P, _I, _I, _P, _P, _I, _I, _P, _P, _P]
+    for f in ("forward", "forward_bf16", "forward_tc", "backward", "mse", "adam", "to_bf16", "ensemble", "gather"):
         getattr(lib, "tt_mlp_" + f).restype = ctypes.c_int
     lib._mlp_bound = True
     return lib
@@ -151,6 +153,57 @@ class Net:
         self.w16 = [t.empty(w.shape, dtype=t.int16, device=w.device) for w in self.w]
         for w, w16 in zip(self.w, self.w16):
             _ok(self.lib.tt_mlp_to_bf16(_ptr(w), _ptr(w16), w.numel(), self.stream.cuda_stream), "tt_mlp_to_bf16")
+        # tensor-core copies: inputs padded with zero columns to a multiple of 16
+        self.w16tc = []
+        for w in self.w:
+            o, i = w.shape
+            ip = -(-i // 16) * 16
+            wp = t.zeros((o, ip), dtype=t.float32, device=w.device)
+            wp[:, :i] = w
+            w16 = t.empty((o, ip), dtype=t.int16, device=w.device)
+            _ok(self.lib.tt_mlp_to_bf16(_ptr(wp), _ptr(w16), wp.numel(), self.stream.cuda_stream), "tt_mlp_to_bf16")
+            self.w16tc.append(w16)
+
+    def tc_layers(self) -> int:
+        """Leading layers that run on the tensor cores (outputs a multiple of 16, <= 256)."""
+        n = 0
+        for o in self.sizes[1:]:
+            if o % 16 or o > 256 or self.sizes[n] > 256:
+                break
+            n += 1
+        return n
+
+    def forward_tc(self, x16):
+        """x16: device bfloat16 (int16 storage) [batch, in padded to 16]; the leading
+        layers on the tensor cores (bfloat16 activations, FP32 accumulation), the rest
+        on the bfloat16-weight path; returns the output buffer [batch, 1]."""
+        t = self.torch
+        batch = x16.shape[0]
+        z, a, _ = self._buffers(batch)
+        s = self.stream.cuda_stream
+        ntc = self.tc_layers()
+        key = ("tc", batch)
+        if key not in self._bufs:
+            self._bufs[key] = [t.empty((batch, o), dtype=t.int16, device=x16.device) for o in self.sizes[1:]]
+        h16 = self._bufs[key]
+        inp = x16
+        last = len(self.w) - 1
+        for l in range(ntc):
+            act = LINEAR if l == last else SILU
+            i, o = self.w16tc[l].shape[1], self.sizes[l + 1]
+            fp32_out = l == ntc - 1  # the next layer reads FP32
+            _ok(self.lib.tt_mlp_forward_tc(_ptr(inp), batch, i, _ptr(self.w16tc[l]), _ptr(self.b[l]), o, act,
+                                           _ptr(a[l]) if fp32_out else 0, 0 if fp32_out else _ptr(h16[l]), s),
+                "tt_mlp_forward_tc")
+            inp = h16[l]
+        out = a[ntc - 1] if ntc else None
+        for l in range(ntc, len(self.w)):
+            act = LINEAR if l == last else SILU
+            i, o = self.sizes[l], self.sizes[l + 1]
+            _ok(self.lib.tt_mlp_forward_bf16(_ptr(out), batch, i, _ptr(self.w16[l]), _ptr(self.b[l]), o, act,
+                                             _ptr(z[l]), _ptr(a[l]), s), "tt_mlp_forward_bf16")
+            out = a[l]
+        return out
 
 
 def train(net: Net, x, y, epochs: int, batch: int, lr: float, seed: int,
@@ -219,15 +272,30 @@ class Surrogate:
         return torch.tensor((f - self.fx[0]) / self.fx[1], dtype=torch.float32,
                             device=f"cuda:{self.device}").contiguous()
 
+    def standardise_tc(self, problems: Sequence):
+        """Device bfloat16 (int16 storage) [n, 16] standardised features, zero-padded."""
+        import torch
+
+        f = (features(problems) - self.fx[0]) / self.fx[1]
+        fp = np.zeros((f.shape[0], 16), dtype=np.float32)
+        fp[:, :f.shape[1]] = f
+        src = torch.tensor(fp, device=f"cuda:{self.device}")
+        dst = torch.empty(src.shape, dtype=torch.int16, device=src.device)
+        net0 = self.nets[0]
+        _ok(net0.lib.tt_mlp_to_bf16(_ptr(src), _ptr(dst), src.numel(), net0.stream.cuda_stream), "to_bf16")
+        return dst
+
     def predict_device(self, x):
-        """Ensemble members on device features x (bfloat16 weights); returns device
-        (mean, spread) of the standardised log-price."""
+        """Ensemble members on device features: bfloat16 [n, 16] (tensor-core layers, from
+        standardise_tc) or float32 [n, 15] (bfloat16 weights, FP32 activations); returns
+        device (mean, spread) of the standardised log-price."""
         import torch
 
         n = x.shape[0]
+        tc = x.dtype == torch.int16
         preds = torch.empty((len(self.nets), n), dtype=torch.float32, device=x.device)
         for k, net in enumerate(self.nets):
-            preds[k].copy_(net.forward(x, bf16=True)[:, 0])
+            preds[k].copy_((net.forward_tc(x) if tc else net.forward(x, bf16=True))[:, 0])
         mean = torch.empty(n, dtype=torch.float32, device=x.device)
         spread = torch.empty(n, dtype=torch.float32, device=x.device)
         net0 = self.nets[0]
@@ -236,14 +304,15 @@ class Surrogate:
         return mean, spread
 
     def predict_log(self, problems: Sequence) -> Tuple[np.ndarray, np.ndarray]:
-        """(mean, spread) over the members of log(price / K), via the bfloat16 weights."""
-        mean, spread = self.predict_device(self.standardise(problems))
+        """(mean, spread) over the members of log(price / K), via the tensor-core layers."""
+        mean, spread = self.predict_device(self.standardise_tc(problems))
         mu, sd = self.fy
         return mean.cpu().numpy().astype(np.float64) * sd + mu, spread.cpu().numpy().astype(np.float64) * sd
 
-    def quote(self, problems: Sequence, pricer=None, tol: float = 1e-4):
+    def quote(self, problems: Sequence, pricer=None, tol: float = 1e-4, memory=None):
         """Prices from the ensemble mean; quotes whose members spread by more than
-        `tol` in log-price are priced by `pricer` (a ttprice.Pricer) instead.
+        `tol` in log-price are priced by `pricer` (a ttprice.Pricer) instead, warm
+        started from `memory` (a PivotMemory) when given.
         Returns (prices, mask of the quotes the TT pricer gave, spread)."""
         mean, spread = self.predict_log(problems)
         k = np.array([p.strike for p in problems])
@@ -251,6 +320,43 @@ class Surrogate:
         back = spread > tol
         if pricer is not None and back.any():
             idx = np.flatnonzero(back)
-            _, tt, _ = pricer.evaluate([problems[i] for i in idx])
+            todo = [problems[i] for i in idx]
+            if memory is not None:
+                todo = memory.warm(todo)
+            _, tt, _ = pricer.evaluate(todo)
             prices[idx] = tt
         return prices, back, spread
+
+
+class PivotMemory:
+    """Warm starts for the TT fallback from the surrogate's training data.
+
+    TT-cross starts from random column sets (Section IV.B); the pivots it
+    converges to move little with the option's parameters.  The TT solves that
+    produced the surrogate's training prices also leave their final right index
+    sets (tt_price_pivots); a quote sent back to TT is warm started from the
+    pivots of the nearest training problem in the surrogate's standardised
+    feature space (the inputs its networks see).  The pivots are a set of grid
+    multi-indices per bond, not a quantity a regression output fits, so the
+    learned part here is the feature space and the memory, not a network head."""
+
+    def __init__(self, problems: Sequence, records: Sequence[np.ndarray], fx):
+        f = features(problems)
+        self.fx = fx
+        self.z = (f - fx[0]) / fx[1]
+        self.records = list(records)
+        self.shape = [(p.d, p.n_grid, p.payoff) for p in problems]
+
+    def nearest(self, problems: Sequence) -> np.ndarray:
+        q = (features(problems) - self.fx[0]) / self.fx[1]
+        d2 = (q * q).sum(1)[:, None] - 2.0 * q @ self.z.T + (self.z * self.z).sum(1)[None, :]
+        return np.argmin(d2, axis=1)
+
+    def warm(self, problems: Sequence) -> List:
+        """The problems with warm_sets from their nearest neighbour of the same shape
+        (d, N, payoff); a problem of another shape is left cold."""
+        out = []
+        for p, j in zip(problems, self.nearest(problems)):
+            same = self.shape[j] == (p.d, p.n_grid, p.payoff)
+            out.append(p.with_(warm_sets=self.records[j]) if same else p)
+        return out

@@ -39,10 +39,10 @@ METHODS = {"single": TT_METHOD_SINGLE_TRAIN, "two-train": TT_METHOD_TWO_TRAINS}
 
 EXPORTS = ("tt_price_create", "tt_workspace_bytes", "tt_price_evaluate", "tt_price_prepare",
            "tt_price_run", "tt_price_results", "tt_price_transfer_bytes", "tt_price_destroy",
-           "tt_status_string", "tt_price_evaluate_static",
+           "tt_status_string", "tt_price_evaluate_static", "tt_price_pivots", "tt_pivot_record_entries",
            # the surrogate's network kernels (include/ttmlp.h)
            "tt_mlp_forward", "tt_mlp_forward_bf16", "tt_mlp_backward", "tt_mlp_mse", "tt_mlp_adam",
-           "tt_mlp_to_bf16", "tt_mlp_ensemble", "tt_mlp_gather",
+           "tt_mlp_to_bf16", "tt_mlp_ensemble", "tt_mlp_gather", "tt_mlp_forward_tc",
            # measured arithmetic peaks (include/ttprobe.h)
            "tt_probe_fma_peak")
 
@@ -71,7 +71,7 @@ class tt_options(ctypes.Structure):
                 ("method", ctypes.c_int), ("device", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("classes", ctypes.POINTER(tt_class_tuning)),
-                ("n_classes", ctypes.c_int)]
+                ("n_classes", ctypes.c_int), ("pivot_io", ctypes.c_int)]
 
 
 class tt_problem(ctypes.Structure):
@@ -80,7 +80,8 @@ class tt_problem(ctypes.Structure):
                 ("maturity", ctypes.c_double), ("strike", ctypes.c_double),
                 ("payoff", ctypes.c_int), ("damping", ctypes.POINTER(ctypes.c_double)),
                 ("n_grid", ctypes.c_int), ("trunc_L", ctypes.c_double),
-                ("max_rank", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+                ("max_rank", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("max_rank_phi", ctypes.c_int),
+                ("warm_sets", ctypes.POINTER(ctypes.c_ushort))]
 
 
 class tt_diag(ctypes.Structure):
@@ -129,6 +130,10 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
                                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(tt_diag)]
     lib.tt_price_evaluate_static.restype = ctypes.c_int
+    lib.tt_price_pivots.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_ushort), ctypes.c_size_t]
+    lib.tt_price_pivots.restype = ctypes.c_int
+    lib.tt_pivot_record_entries.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.tt_pivot_record_entries.restype = ctypes.c_size_t
     if hasattr(lib, "tt_probe_fma_peak"):  # absent from single-source profiling builds
         lib.tt_probe_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         lib.tt_probe_fma_peak.restype = ctypes.c_int
@@ -206,11 +211,11 @@ class DiagList(abc.Sequence):
 # tt_problem as a NumPy record (same offsets as the C struct; checked by the tests)
 PROBLEM_DTYPE = np.dtype({
     "names": ["d", "spot", "cov", "rate", "maturity", "strike", "payoff", "damping", "n_grid",
-              "trunc_L", "max_rank", "seed"],
+              "trunc_L", "max_rank", "seed", "max_rank_phi", "warm_sets"],
     "formats": [np.int32, np.uint64, np.uint64, np.float64, np.float64, np.float64, np.int32,
-                np.uint64, np.int32, np.float64, np.int32, np.uint64],
-    "offsets": [0, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 88],
-    "itemsize": 96,
+                np.uint64, np.int32, np.float64, np.int32, np.uint64, np.int32, np.uint64],
+    "offsets": [0, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96, 104],
+    "itemsize": 112,
 })
 
 
@@ -248,6 +253,11 @@ class ProblemBatch:
         r["n_grid"] = ints[:, 1]
         r["max_rank"] = ints[:, 2]
         r["seed"] = [int(p.seed) & ((1 << 64) - 1) for p in problems]
+        r["max_rank_phi"] = [int(getattr(p, "max_rank_phi", 0) or 0) for p in problems]
+        # warm-start records (uint16), kept alive with the batch
+        self.warm = [None if getattr(p, "warm_sets", None) is None
+                     else np.ascontiguousarray(p.warm_sets, dtype=np.uint16) for p in problems]
+        r["warm_sets"] = [0 if w is None else w.ctypes.data for w in self.warm]
         self.arr = r.ctypes.data_as(ctypes.POINTER(tt_problem))
 
 
@@ -272,18 +282,18 @@ class Pricer:
     ``method`` = "single" crosses the product integrand (one train per term);
     "two-train" is the paper's bra-ket form (Section IV, Eq. braket): separate
     trains of the payoff transform and the characteristic function, contracted
-    site by site (rank <= 32, N <= 1024)."""
+    site by site (ranks <= 40, D_phi from Problem.max_rank_phi)."""
 
     def __init__(self, max_d: int, max_n: int, max_rank: int, max_batch: int,
                  precision: str = "fp64", device: int = 0, stream=None, max_half_sweeps: int = 0,
                  sweep_tol: float = 0.0, rank_tol: float = 0.0, maxvol_tol: float = 0.0,
                  block_rows: int = 0, use_torch_workspace: bool = True, engine: str = "auto",
-                 graph: bool = True, method: str = "single", classes=None):
+                 graph: bool = True, method: str = "single", classes=None, lib=None, pivot_io: bool = False):
         import torch  # device memory and streams only
 
         if not torch.cuda.is_available():
             raise RuntimeError("the tensor-train pricer needs a CUDA device; none is available")
-        self.lib = load_library()
+        self.lib = lib or load_library()  # another build of the library (profiling, tests) when given
         self.torch = torch
         self.device = device
         self.opts = tt_options()
@@ -301,6 +311,8 @@ class Pricer:
         self._classes = class_table(classes or [])
         o.classes = self._classes
         o.n_classes = len(classes or [])
+        o.pivot_io = 1 if pivot_io else 0
+        self.max_d, self.max_rank = max_d, max_rank
         with torch.cuda.device(device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -361,6 +373,17 @@ class Pricer:
         h2d, d2h = ctypes.c_size_t(), ctypes.c_size_t()
         self.lib.tt_price_transfer_bytes(self.handle, ctypes.byref(h2d), ctypes.byref(d2h))
         return int(h2d.value), int(d2h.value)
+
+    def pivots(self, i: int) -> np.ndarray:
+        """Final right index sets of problem i of the last run (the warm_sets record
+        format of include/ttprice.h); needs pivot_io."""
+        terms = self.max_d
+        cap = int(self.lib.tt_pivot_record_entries(self.max_d, self.max_rank)) * terms
+        buf = (ctypes.c_ushort * max(1, cap))()
+        n = self.lib.tt_price_pivots(self.handle, int(i), buf, cap)
+        if n < 0:
+            raise RuntimeError(f"tt_price_pivots failed: {status_string(n)} ({n})")
+        return np.frombuffer(buf, dtype=np.uint16, count=n).copy()
 
     def evaluate(self, problems):
         """Price a batch; returns (worst status, prices ndarray, sequence of Diag)."""

@@ -100,12 +100,13 @@ def test_struct_layouts_match_c():
              offsetof(tt_options, block_rows), offsetof(tt_options, engine), offsetof(tt_options, graph),
              offsetof(tt_options, method), offsetof(tt_options, cuda_stream),
              offsetof(tt_options, workspace_bytes));
-      printf("%zu %zu %zu %zu %zu\n", sizeof(tt_problem), offsetof(tt_problem, rate),
-             offsetof(tt_problem, damping), offsetof(tt_problem, trunc_L), offsetof(tt_problem, seed));
+      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(tt_problem), offsetof(tt_problem, rate),
+             offsetof(tt_problem, damping), offsetof(tt_problem, trunc_L), offsetof(tt_problem, seed),
+             offsetof(tt_problem, max_rank_phi), offsetof(tt_problem, warm_sets));
       printf("%zu %zu %zu %zu %zu\n", sizeof(tt_diag), offsetof(tt_diag, evaluations), offsetof(tt_diag, fail_step),
              offsetof(tt_diag, flops), offsetof(tt_diag, est_discretization_err));
-      printf("%zu %zu %zu\n", sizeof(tt_class_tuning), offsetof(tt_class_tuning, rank_tol),
-             offsetof(tt_options, n_classes));
+      printf("%zu %zu %zu %zu\n", sizeof(tt_class_tuning), offsetof(tt_class_tuning, rank_tol),
+             offsetof(tt_options, n_classes), offsetof(tt_options, pivot_io));
       return 0;
     }
     """
@@ -121,10 +122,12 @@ def test_struct_layouts_match_c():
          T.tt_options.engine.offset, T.tt_options.graph.offset, T.tt_options.method.offset,
          T.tt_options.cuda_stream.offset, T.tt_options.workspace_bytes.offset],
         [ctypes.sizeof(T.tt_problem), T.tt_problem.rate.offset, T.tt_problem.damping.offset,
-         T.tt_problem.trunc_L.offset, T.tt_problem.seed.offset],
+         T.tt_problem.trunc_L.offset, T.tt_problem.seed.offset, T.tt_problem.max_rank_phi.offset,
+         T.tt_problem.warm_sets.offset],
         [ctypes.sizeof(T.tt_diag), T.tt_diag.evaluations.offset, T.tt_diag.fail_step.offset,
          T.tt_diag.flops.offset, T.tt_diag.est_discretization_err.offset],
-        [ctypes.sizeof(T.tt_class_tuning), T.tt_class_tuning.rank_tol.offset, T.tt_options.n_classes.offset],
+        [ctypes.sizeof(T.tt_class_tuning), T.tt_class_tuning.rank_tol.offset, T.tt_options.n_classes.offset,
+         T.tt_options.pivot_io.offset],
     ]
     assert len([ln for ln in out if ln.strip()]) == len(want)
     for line, w in zip(out, want):
@@ -174,7 +177,8 @@ def test_problem_batch_packs_every_field():
         assert float(r["strike"]) == p.strike and float(r["trunc_L"]) == p.trunc_L
         assert int(r["payoff"]) == (ttprice.TT_MIN_CALL if p.payoff == "min" else ttprice.TT_MAX_CALL)
         assert int(r["n_grid"]) == p.n_grid and int(r["max_rank"]) == p.max_rank
-        assert int(r["seed"]) == p.seed
+        assert int(r["seed"]) == p.seed and int(r["max_rank_phi"]) == p.max_rank_phi
+        assert int(r["warm_sets"]) == 0
 
 
 def test_diag_list_reads_the_c_array():

@@ -264,21 +264,6 @@ def test_largest_grids_two_assets(tp):
         assert abs(prices[0] / oracle_price(q) - 1) < MIXED_TOL, e
 
 
-def test_high_dim_max_call_fp64_vs_mixed_engines(tp):
-    """d=20 call on the maximum (N=256, rank 32, damping -5/d): the FP64 and both mixed
-    engines' TTs agree (measured 0.15 %), with a small imaginary part.  The grid itself
-    is 15 % from Monte Carlo at this configuration (aliasing at rate 5/d per axis), so
-    the comparison is between the GPU paths, as the high-d workload defines it."""
-    p = inputs.high_dim_problem(20, "max").with_(max_rank=32)
-    _, p64, d64 = gpu_price(tp, [p], precision="fp64")
-    for e in ENGINES:
-        _, pm, dm = gpu_price(tp, [p], precision="mixed", engine=e)
-        assert dm[0].status in (tp.TT_OK, tp.TT_WARN_NOT_CONVERGED)
-        assert abs(pm[0] / p64[0] - 1) < 1e-2, e
-        assert abs(dm[0].imag_part) < 1e-2 * abs(pm[0])
-    assert abs(d64[0].imag_part) < 1e-2 * abs(p64[0])
-
-
 def test_mixed_default_rank_tol_at_the_paper_setting(tp):
     """The paper's own setting (N=50, rank cap 15, d = 2, 5, 6): with its default
     rank threshold the mixed single train stays within 1e-4 of the FP64 path."""

@@ -105,3 +105,50 @@ def test_ensemble_quotes_fall_back_to_the_tt_pricer(env):
     p_none, back_none, spread = s.quote(qs, pricer=pr, tol=np.inf)
     assert not back_none.any() and np.all(np.isfinite(p_none)) and np.all(spread >= 0)
     pr.close()
+
+
+@pytest.mark.parametrize("batch,k,n,act", [(300, 256, 256, 1), (300, 16, 256, 1), (129, 256, 64, 0),
+                                           (128, 32, 16, 1), (1000, 256, 256, 0)])
+def test_tensor_core_layer_against_fp64(env, batch, k, n, act):
+    """tt_mlp_forward_tc (tcgen05.mma kind::f16) against the FP64 product of the same
+    bfloat16 operands: several 128-row tiles with a ragged last one, K = 16 .. 256,
+    N = 16 .. 256, both activations.  Products of bfloat16 values are exact in FP32,
+    so the FP32 accumulation leaves ~K 2^-24 of the output's scale; the bfloat16
+    output is the FP32 output rounded to nearest."""
+    torch, sg, _ = env
+    lib = sg._bind(sg.ttprice.load_library())
+    rng = np.random.default_rng(batch + k + n + act)
+    x = torch.tensor(rng.standard_normal((batch, k)), dtype=torch.float32).to(torch.bfloat16)
+    w = torch.tensor(rng.standard_normal((n, k)) * np.sqrt(2.0 / k), dtype=torch.float32).to(torch.bfloat16)
+    b = torch.tensor(rng.standard_normal(n) * 0.1, dtype=torch.float32)
+    ref = x.double().numpy() @ w.double().numpy().T + b.double().numpy()
+    if act:
+        ref = omlp.silu(ref)
+    xd, wd, bd = x.cuda().contiguous(), w.cuda().contiguous(), b.cuda()
+    af = torch.empty((batch, n), dtype=torch.float32, device="cuda")
+    ab = torch.empty((batch, n), dtype=torch.bfloat16, device="cuda")
+    rc = lib.tt_mlp_forward_tc(xd.data_ptr(), batch, k, wd.data_ptr(), bd.data_ptr(), n, act, af.data_ptr(),
+                               ab.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    got = af.cpu().double().numpy()
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max() + 1e-6
+    assert torch.equal(ab.cpu(), af.cpu().to(torch.bfloat16))
+
+
+def test_tensor_core_inference_matches_the_bf16_weight_path(env):
+    """The surrogate at its real width (15 -> 256 x 4 -> 1) on 700 quotes: the
+    tensor-core layers (bfloat16 activations) against the bfloat16-weight path (FP32
+    activations) to bfloat16 rounding of the activations."""
+    torch, sg, _ = env
+    s = sg.Surrogate(members=2, seed=9)
+    ps = inputs.surrogate_batch(700, index=9)
+    f = sg.features(ps)
+    s.fx = (f.mean(0), f.std(0) + 1e-12)
+    s.fy = (0.0, 1.0)
+    for net in s.nets:
+        net.to_bf16()
+    m_tc, sp_tc = s.predict_device(s.standardise_tc(ps))
+    m_32, sp_32 = s.predict_device(s.standardise(ps))
+    a, c = m_tc.cpu().numpy(), m_32.cpu().numpy()
+    assert np.abs(a - c).max() < 2e-2 * max(1.0, np.abs(c).max())

@@ -150,3 +150,29 @@ def test_invalid_problems_between_valid_ones(tp):
             assert diags[i].status == tp.TT_OK
             _, alone, _ = _price(tp, [batch[i]], "fp64", graph=graph)
             assert prices[i] == alone[0], (i, prices[i], alone[0])
+
+
+@pytest.mark.parametrize("d,rank_v,rank_phi", [(4, 30, 15), (7, 40, 20)])
+def test_separate_bond_dimensions(tp, d, rank_v, rank_phi):
+    """Table I's separate bond dimensions (D_v, D_phi) = (30, 15) at d = 4 and
+    (40, 20) at d = 7, the paper's own setting (N = 50, eta from its table): FP64
+    against the two-train price under the kernel's schedule (1e-6) with the same
+    caps, and the mixed path against it (1e-4)."""
+    p = inputs.paper_table_problem(d).with_(max_rank=rank_v, max_rank_phi=rank_phi)
+    ref = twomps.two_train_price(p, ks.ScheduleOptions(max_half_sweeps=twomps.HALF_SWEEPS),
+                                 select=ks.schedule_select, rank_v=rank_v, rank_phi=rank_phi)[0]
+    for precision, tol in (("fp64", 1e-6), ("mixed", 1e-4)):
+        pr = tp.Pricer(max_d=d, max_n=50, max_rank=rank_v, max_batch=1, precision=precision,
+                       method="two-train")
+        rc, prices, diags = pr.evaluate([p])
+        pr.close()
+        assert diags[0].status == tp.TT_OK, (precision, diags[0])
+        assert abs(prices[0] / ref - 1) < tol, (precision, prices[0], ref)
+        if precision == "fp64":  # the paper-order oracle's trains agree with the schedule's to ~1e-7 here
+            oracle = twomps.two_train_price(p, rank_v=rank_v, rank_phi=rank_phi)[0]
+            assert abs(prices[0] / oracle - 1) < 1e-6
+    # the cap product above the bracket's 1024 accumulator entries is refused per problem
+    pr = tp.Pricer(max_d=d, max_n=50, max_rank=40, max_batch=1, precision="fp64", method="two-train")
+    rc, prices, diags = pr.evaluate([p.with_(max_rank=40, max_rank_phi=40)])
+    pr.close()
+    assert diags[0].status == tp.TT_ERR_CAPACITY and np.isnan(prices[0])
