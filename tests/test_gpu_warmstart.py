@@ -50,10 +50,15 @@ def test_pivot_record_round_trip(env):
         assert np.all(rec[off + 1:off + 1 + c * (d - k)] < p.n_grid)
         off += 1 + c * (d - k)
     assert off == rec.size
-    # the same problem from its own converged pivots: as many half-sweeps at most, same price
+    # the same problem from its own final pivots: as many half-sweeps at most, and a
+    # train no further from the exact grid sum.  This option is far out of the money
+    # (price 0.56 on spots near 100): both trains carry a few 1e-4 of relative TT error
+    # at rank 32 (3e-6 of the spot), so they are compared through the exact sum.
     v1, d1, _ = _solve(tp, [p.with_(warm_sets=rec)])
     assert d1[0].half_sweeps <= d0[0].half_sweeps
-    assert abs(v1[0] / v0[0] - 1) < 1e-4  # two trains of one tensor, each within its TT error
+    exact = grid_sum.grid_sum_for(p)[0]
+    e0, e1 = abs(v0[0] / exact - 1), abs(v1[0] / exact - 1)
+    assert e0 < 2e-3 and e1 <= max(1.5 * e0, 1e-5), (e0, e1)
 
 
 def test_malformed_warm_records_are_refused(env):
