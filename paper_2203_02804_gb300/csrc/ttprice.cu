@@ -878,8 +878,10 @@ SmemLayout make_smem(const tt_options& o, bool f64) {
   const int rs = f64 ? 8 : 4, cs = 2 * rs;
   const int r = o.max_rank, b = o.block_rows, n = o.max_n, d = o.max_d;
   int sw_elems = std::max((r + std::max(b, 128)) * r, 2 * r * r);
-  // the FP64 interpolation solve: [P^T | y] (r x (r+1) complex doubles) and its reduction scratch
+  // the FP64 interpolation solve: [P^T | y] (r x (r+1) complex doubles) and its reduction
+  // scratch; its refinement: P, w, y and the residual (r (r+3) complex doubles), 3 kWarps doubles
   sw_elems = std::max(sw_elems, (r * (r + 1) * 16 + 2 * ttp::kWarps * 12 + cs - 1) / cs);
+  sw_elems = std::max(sw_elems, (r * (r + 3) * 16 + 3 * ttp::kWarps * 8 + cs - 1) / cs);
   const int kp = ttp::tc::pad16(r);
   const bool tcore = o.engine == TT_ENGINE_TENSOR_CORES;
   // tensor cores: kTcBufs buffers of four 128-row planes of one kTcChunk-column chunk
@@ -1965,11 +1967,11 @@ extern "C" int tt_price_evaluate_static(const tt_problem* probs, int count, int 
 #ifdef TTP_PHASE_TIMERS
 // Profiling builds only (not part of the ABI in include/ttprice.h): read and
 // optionally clear the per-phase cycle counters of the current device.
-extern "C" int tt_phase_cycles(unsigned long long* out16, int reset) {
-  if (out16 && cudaMemcpyFromSymbol(out16, ttp::g_phase_cycles, 16 * sizeof(unsigned long long)) != cudaSuccess)
+extern "C" int tt_phase_cycles(unsigned long long* out24, int reset) {
+  if (out24 && cudaMemcpyFromSymbol(out24, ttp::g_phase_cycles, 24 * sizeof(unsigned long long)) != cudaSuccess)
     return TT_ERR_CUDA;
   if (reset) {
-    const unsigned long long z[16] = {0};
+    const unsigned long long z[24] = {0};
     if (cudaMemcpyToSymbol(ttp::g_phase_cycles, z, sizeof(z)) != cudaSuccess) return TT_ERR_CUDA;
   }
   return TT_OK;

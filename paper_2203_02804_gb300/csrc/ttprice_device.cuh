@@ -1001,12 +1001,24 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
     // never maxvol candidates (excluding them only guards against FP32 drift)
     unsigned char* inw = reinterpret_cast<unsigned char*>(x.scand);
     for (int r = tid; r < bs; r += kThreads) inw[r] = 0;
-    // two threads per row (128 rows per pass), each the row's every other kept column
+    // two threads per row (128 rows per pass), each the row's every other kept
+    // column, four independent points at a time (loads before stores)
     for (int rr = tid & 127; rr < bs; rr += 128) {
       const int g = rs + rr;
       const RowTab<R> rt = row_tab(x, g % N);
       const int o = g / N;
-      for (int t = tid >> 7; t < rho; t += 2) A[t * b + rr] = eval_row_point(x, rt, o, x.jp[t]);
+      int t = tid >> 7;
+      for (; t + 6 < rho; t += 8) {
+        const cpx<R> v0 = eval_row_point(x, rt, o, x.jp[t]);
+        const cpx<R> v1 = eval_row_point(x, rt, o, x.jp[t + 2]);
+        const cpx<R> v2 = eval_row_point(x, rt, o, x.jp[t + 4]);
+        const cpx<R> v3 = eval_row_point(x, rt, o, x.jp[t + 6]);
+        A[t * b + rr] = v0;
+        A[(t + 2) * b + rr] = v1;
+        A[(t + 4) * b + rr] = v2;
+        A[(t + 6) * b + rr] = v3;
+      }
+      for (; t < rho; t += 2) A[t * b + rr] = eval_row_point(x, rt, o, x.jp[t]);
     }
     if (tid == 0) x.flops += 24.0 * bs * rho + (frozen ? 0.0 : 8.0 * (double)bs * rho * rho);
     __syncthreads();
@@ -1511,6 +1523,162 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// sum over aligned groups of g consecutive lanes (g a power of two <= 32)
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int g) {
+  for (int off = g >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// P^{-1}[t][s] as maxvol leaves it: R-precision, updated through its swaps
+template <typename R, bool TC>
+__device__ __forceinline__ cpx<R> minv_at(const Ctx<R>& x, int kp, int t, int s) {
+  if constexpr (TC) {
+    return minv_get(x, kp, t, s);
+  } else {
+    return x.M[t * x.rall + s];
+  }
+}
+
+constexpr int kRefineIters = 8;
+
+// y P = w (w = v S, the contraction's row vector) by iterative refinement on
+// maxvol's running inverse M ~ P^{-1}: y_0 = 0, r_0 = w; then d = r M in R,
+// y += d and r = w - y P in FP64, until |d|max <= tol |y|max.  The residual
+// is formed in FP64 from P's exact entries, so the iterates converge to the
+// FP64 solution of the same system as long as |I - M P| < 1 (Wilkinson's
+// mixed-precision refinement); each step gains about -log10 |I - M P| digits.
+// The right-hand side is scaled by a power of two before rounding to R, so an
+// FP64 chain vector far outside R's range keeps its relative precision.
+// Returns false (nothing written) when the corrections stop shrinking by at
+// least half per step before reaching tol, or do not reach it within
+// kRefineIters steps: the caller then eliminates instead.  Scratch: r(r+3)
+// complex doubles and 3 kWarps doubles in sw.
+template <typename R, bool TC>
+__device__ bool chain_refine(Ctx<R>& x, int no, int rho) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tpc = rho <= 32 ? 8 : 4;  // threads per output (rho <= 64)
+  const int out = tid / tpc, part = tid % tpc;
+  // every lane of a warp reaches each shuffle below (the loop counts are
+  // block-uniform); lanes without an output carry zeros through the sums
+  const bool own = out < rho;
+  const int kp = tc::pad16(rho);
+  double2* Pd = reinterpret_cast<double2*>(x.sw);  // [rho][rho], P's entries in FP64
+  double2* w = Pd + rho * rho;
+  double2* y = w + rho;
+  double2* r = y + rho;
+  double* red = reinterpret_cast<double*>(r + rho);  // 3 kWarps: |d|, |y|, then |w| apart
+  // stop at |d|max <= 1e-9 |y|max with an R = FP32 inverse (two orders below the
+  // FP32 rounding of the fiber entries P and w come from), 1e-12 with an FP64 one
+  const double tol2 = sizeof(R) == 4 ? 1e-18 : 1e-24;
+  // w = v S over the outer indices, FP64
+  double2 s = make_double2(0.0, 0.0);
+  if (own) {
+    for (int o = part; o < no; o += tpc) {
+      const double2 v = x.vchain[o], a = x.sacc[o * x.rall + out];
+      s.x += v.x * a.x - v.y * a.y;
+      s.y += v.x * a.y + v.y * a.x;
+    }
+  }
+  s.x = group_sum(s.x, tpc);
+  s.y = group_sum(s.y, tpc);
+  double wn = 0.0;
+  if (own && part == 0) {
+    w[out] = s;
+    r[out] = s;
+    y[out] = make_double2(0.0, 0.0);
+    wn = s.x * s.x + s.y * s.y;
+  }
+  for (int idx = tid; idx < rho * rho; idx += kThreads) {
+    const cpx<R> p = x.P[(idx / rho) * x.rall + idx % rho];
+    Pd[idx] = make_double2((double)p.re, (double)p.im);
+  }
+  for (int off = 16; off > 0; off >>= 1) wn = fmax(wn, __shfl_xor_sync(0xffffffffu, wn, off));
+  if (lane == 0) red[2 * kWarps + warp] = wn;
+  __syncthreads();
+  wn = red[2 * kWarps];
+#pragma unroll
+  for (int q = 1; q < kWarps; ++q) wn = fmax(wn, red[2 * kWarps + q]);
+  if (!(wn > 0.0) || !(wn < INFINITY)) return false;  // block-uniform
+  // r is rounded to R after scaling by 2^-e, |w|max in [2^(e-1), 2^e)
+  int e;
+  frexp(sqrt(wn), &e);
+  const double sc = ldexp(1.0, -e), isc = ldexp(1.0, e);
+  double prev = INFINITY;
+  bool done = false;
+  int it_used = 0;
+  for (int it = 0; it < kRefineIters; ++it) {
+    it_used = it + 1;
+    // d = r M (R precision), output s = out, sum over t
+    R dr = R(0), di = R(0);
+    if (own) {
+      for (int t = part; t < rho; t += tpc) {
+        const double2 rt = r[t];
+        const R ar = (R)(rt.x * sc), ai = (R)(rt.y * sc);
+        const cpx<R> m = minv_at<R, TC>(x, kp, t, out);
+        dr += ar * m.re - ai * m.im;
+        di += ar * m.im + ai * m.re;
+      }
+    }
+    dr = group_sum(dr, tpc);
+    di = group_sum(di, tpc);
+    double dn = 0.0, yn = 0.0;
+    if (own && part == 0) {
+      const double ddr = (double)dr * isc, ddi = (double)di * isc;
+      double2 yv = y[out];
+      yv.x += ddr;
+      yv.y += ddi;
+      y[out] = yv;
+      dn = ddr * ddr + ddi * ddi;
+      yn = yv.x * yv.x + yv.y * yv.y;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      dn = fmax(dn, __shfl_xor_sync(0xffffffffu, dn, off));
+      yn = fmax(yn, __shfl_xor_sync(0xffffffffu, yn, off));
+    }
+    if (lane == 0) {
+      red[warp] = dn;
+      red[kWarps + warp] = yn;
+    }
+    __syncthreads();  // also publishes y
+    dn = red[0];
+    yn = red[kWarps];
+#pragma unroll
+    for (int q = 1; q < kWarps; ++q) {
+      dn = fmax(dn, red[q]);
+      yn = fmax(yn, red[kWarps + q]);
+    }
+    if (!(dn < INFINITY) || !(yn < INFINITY)) break;  // block-uniform
+    if (dn <= tol2 * yn) {
+      done = true;
+      break;
+    }
+    if (!(dn <= 0.25 * prev)) break;
+    prev = dn;
+    // r = w - y P (FP64), output t = out, sum over j
+    double2 q2 = make_double2(0.0, 0.0);
+    if (own) {
+      for (int j = part; j < rho; j += tpc) {
+        const double2 yv = y[j], p = Pd[j * rho + out];
+        q2.x += yv.x * p.x - yv.y * p.y;
+        q2.y += yv.x * p.y + yv.y * p.x;
+      }
+    }
+    q2.x = group_sum(q2.x, tpc);
+    q2.y = group_sum(q2.y, tpc);
+    if (own && part == 0) r[out] = make_double2(w[out].x - q2.x, w[out].y - q2.y);
+    __syncthreads();
+  }
+  if (done)
+    for (int t = tid; t < rho; t += kThreads) x.vchain[t] = y[t];
+  (void)it_used;
+  TTP_COUNT(16, 1);
+  TTP_COUNT(17, done ? 0 : 1);
+  TTP_COUNT(18, it_used);
+  __syncthreads();
+  return done;
+}
+
 // y P = w by Gaussian elimination with partial pivoting on [P^T | w^T], FP64.
 // Rows stay in place: the pivot of column c is the unused row with the largest
 // |entry|^2 (order[c]); the other unused rows subtract their multiple of it at
@@ -1519,8 +1687,14 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 // collect its argmax, so an elimination step costs one block barrier.  The pivot
 // row's first thread forms 1/pivot meanwhile, and warp 0 back-substitutes by
 // shuffles alone.
-template <typename R>
+template <typename R, bool TC>
 __device__ void chain_solve(Ctx<R>& x, int no, int rho) {
+  __syncthreads();  // maxvol's last reads of sw are done; its failure flag is visible
+  if (!x.misc[MISC_FAIL] && chain_refine<R, TC>(x, no, rho)) {
+    // the solve's algorithmic count is elimination's, however it is reached
+    if (threadIdx.x == 0) x.flops += 8.0 * (double)no * rho + 8.0 * (double)rho * rho * rho / 3.0;
+    return;
+  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int t = tid; t < rho; t += kThreads) {
     double2 y = make_double2(0.0, 0.0);
@@ -1684,7 +1858,7 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
     maxvol_refine(x, m, no, rho, b, (R)((1.0 + kn.tau) * (1.0 + kn.tau)));
   }
   TTP_TIC(t_ch);
-  chain_solve(x, no, rho);
+  chain_solve<R, TC>(x, no, rho);
   TTP_TOC(t_ch, 10);
   // new index set
   if (dir == DIR_LR) {

@@ -25,14 +25,22 @@ namespace ttp {
 // Optional per-phase cycle counters (profiling builds only: -DTTP_PHASE_TIMERS).
 // Thread 0 of each CTA adds the clock64() span of each phase; the totals show
 // where a CTA's time goes, waits at barriers included.
+// Slots 16..23 count events instead (TTP_COUNT).
 #ifdef TTP_PHASE_TIMERS
-__device__ unsigned long long g_phase_cycles[16];
+__device__ unsigned long long g_phase_cycles[24];
+#define TTP_COUNT(slot, n)                                                               \
+  do {                                                                                   \
+    if (threadIdx.x == 0) atomicAdd(&g_phase_cycles[slot], (unsigned long long)(n));     \
+  } while (0)
 #define TTP_TIC(v) const long long v = clock64()
 #define TTP_TOC(v, slot)                                                            \
   do {                                                                              \
     if (threadIdx.x == 0) atomicAdd(&g_phase_cycles[slot], (unsigned long long)(clock64() - (v))); \
   } while (0)
 #else
+#define TTP_COUNT(slot, n) \
+  do {                     \
+  } while (0)
 #define TTP_TIC(v) \
   do {             \
   } while (0)

@@ -56,17 +56,20 @@ def main():
     pr.run()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    buf = (ctypes.c_ulonglong * 16)()
+    buf = (ctypes.c_ulonglong * 24)()
     L.tt_phase_cycles(buf, 0)
     pr.close()
     nested = {i for i, name in enumerate(PHASES) if name.startswith("  (in ")}
-    tot = sum(v for i, v in enumerate(buf) if i not in nested)
+    tot = sum(v for i, v in enumerate(buf) if i < len(PHASES) and i not in nested)
     print(json.dumps({"workload": "d5-min-call N=128 rank 32", "precision": args.precision,
                       "engine": args.engine, "rank_tol": args.rank_tol or "default",
                       "batch": args.batch, "prices_per_s": args.batch / dt}))
     for i, name in enumerate(PHASES):
         if buf[i]:
             print(f"{name:44s} {buf[i] / args.batch / 1e6:8.3f} Mcycles/price {100 * buf[i] / tot:6.2f}%")
+    if buf[16]:
+        print(f"interpolation solves: {buf[16]}, by refinement {buf[16] - buf[17]} "
+              f"({buf[18] / buf[16]:.2f} steps each), by elimination {buf[17]}")
 
 
 if __name__ == "__main__":
