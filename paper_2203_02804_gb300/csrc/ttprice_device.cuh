@@ -1051,10 +1051,10 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
           vr += __shfl_xor_sync(0xffffffffu, vr, off);
           vi += __shfl_xor_sync(0xffffffffu, vi, off);
         }
-        if (lane == 0) {
-          double2& acc = x.sacc[o * x.rall + t];
-          acc.x += (double)vr;
-          acc.y += (double)vi;
+        if (lane == 0) {  // one add per accumulator and visit: the visits' barriers fix the order
+          double2* acc = &x.sacc[o * x.rall + t];
+          atomicAdd(&acc->x, (double)vr);
+          atomicAdd(&acc->y, (double)vi);
         }
       }
     }
@@ -1370,10 +1370,10 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
             vr += __shfl_xor_sync(0xffffffffu, vr, off);
             vi += __shfl_xor_sync(0xffffffffu, vi, off);
           }
-          if (lane == 0) {
-            double2& acc = x.sacc[o * x.rall + c0 + tl];
-            acc.x += (double)vr;
-            acc.y += (double)vi;
+          if (lane == 0) {  // one add per accumulator and chunk: the barriers fix the order
+            double2* acc = &x.sacc[o * x.rall + c0 + tl];
+            atomicAdd(&acc->x, (double)vr);
+            atomicAdd(&acc->y, (double)vi);
           }
         }
       }
