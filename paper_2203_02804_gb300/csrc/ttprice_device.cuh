@@ -343,8 +343,17 @@ __device__ void column_shifts(Ctx<R>& x, int no, int nc) {
   if constexpr (Num<R>::kScaleColumns) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, N = x.n, m = no * N;
     for (int c = warp; c < nc; c += kWarps) {
-      R mx = R(-3.0e38);
-      for (int r = lane; r < m; r += 32) mx = fmax(mx, eval_logmag(x, r / N, r % N, c));
+      // four independent maxima per lane (a max does not depend on its order)
+      R m0 = R(-3.0e38), m1 = R(-3.0e38), m2 = R(-3.0e38), m3 = R(-3.0e38);
+      int r = lane;
+      for (; r + 96 < m; r += 128) {
+        m0 = fmax(m0, eval_logmag(x, r / N, r % N, c));
+        m1 = fmax(m1, eval_logmag(x, (r + 32) / N, (r + 32) % N, c));
+        m2 = fmax(m2, eval_logmag(x, (r + 64) / N, (r + 64) % N, c));
+        m3 = fmax(m3, eval_logmag(x, (r + 96) / N, (r + 96) % N, c));
+      }
+      for (; r < m; r += 32) m0 = fmax(m0, eval_logmag(x, r / N, r % N, c));
+      R mx = fmax(fmax(m0, m1), fmax(m2, m3));
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
       if (lane == 0) {
@@ -1299,17 +1308,22 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
         const bool live = r < bs;
         const int g = rs + (live ? r : 0);
         const RowTab<R> rt = row_tab(x, g % N);
+        // the row's points first, then the stores (loads before stores: independent)
+        cpx<R> v[kTcChunk / 4];
 #pragma unroll
         for (int jj = 0; jj < kTcChunk / 4; ++jj) {
-          const int tl = (lane & 3) + 4 * jj, t = c0 + tl;
-          cpx<R> v = {R(0), R(0)};
-          if (live && t < rho) v = eval_row_point(x, rt, g / N, x.jp[t]);
+          const int t = c0 + (lane & 3) + 4 * jj;
+          v[jj] = (live && t < rho) ? eval_row_point(x, rt, g / N, x.jp[t]) : cpx<R>{R(0), R(0)};
+        }
+#pragma unroll
+        for (int jj = 0; jj < kTcChunk / 4; ++jj) {
+          const int tl = (lane & 3) + 4 * jj;
           const int off = tc::kmaj(r, tl, kSboA);
-          const R hr = tf32_hi(v.re), hm = tf32_hi(v.im);
+          const R hr = tf32_hi(v[jj].re), hm = tf32_hi(v[jj].im);
           *reinterpret_cast<R*>(pb + off) = hr;
           *reinterpret_cast<R*>(pb + kPlaneA + off) = hm;
-          *reinterpret_cast<R*>(pb + 2 * kPlaneA + off) = v.re - hr;
-          *reinterpret_cast<R*>(pb + 3 * kPlaneA + off) = v.im - hm;
+          *reinterpret_cast<R*>(pb + 2 * kPlaneA + off) = v[jj].re - hr;
+          *reinterpret_cast<R*>(pb + 3 * kPlaneA + off) = v[jj].im - hm;
         }
       }
       TTP_TOC(t_ev8, 14);
@@ -1898,24 +1912,32 @@ __device__ int core_select(Ctx<R>& x, const Knobs& kn, int k, int dir) {
 // end core of a half-sweep: est = sum_o v[o] * sum_i A[(o,i)]
 template <typename R>
 __device__ double2 core_sum(Ctx<R>& x, int k, int dir, double* dscr) {
-  const int tid = threadIdx.x, N = x.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, N = x.n;
   core_states(x, k, dir);
   load_axis_table(x, k);
   const int no = dir == DIR_LR ? x.lsz[k] : x.rsz[k + 1];
   column_shifts(x, no, 1);
+  // one warp per outer index: lanes over the grid index, a warp sum, the
+  // contraction weight; one block sum at the end (lane 0 carries its warp's part)
   double2 est = make_double2(0.0, 0.0);
-  for (int o = 0; o < no; ++o) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int i = tid; i < N; i += kThreads) {
+  for (int o = warp; o < no; o += kWarps) {  // warp-uniform
+    double sx = 0.0, sy = 0.0;
+    for (int i = lane; i < N; i += 32) {
       const cpx<R> a = eval_point(x, o, i, 0);
-      s.x += (double)a.re;
-      s.y += (double)a.im;
+      sx += (double)a.re;
+      sy += (double)a.im;
     }
-    s = block_sum_d2(s, dscr);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, off);
+      sy += __shfl_xor_sync(0xffffffffu, sy, off);
+    }
     const double2 v = x.vchain[o];
-    est.x += v.x * s.x - v.y * s.y;
-    est.y += v.x * s.y + v.y * s.x;
+    est.x += v.x * sx - v.y * sy;
+    est.y += v.x * sy + v.y * sx;
   }
+  if (lane != 0) est = make_double2(0.0, 0.0);
+  est = block_sum_d2(est, dscr);
   if (tid == 0) {
     x.evals += (long long)no * N;
     x.flops += 24.0 * (double)no * N;
