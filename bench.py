@@ -9,8 +9,9 @@ mixed path (FP32 integrand/elimination/maxvol, FP64 phase, solve and sums).
 
 Prints one JSON line.  `value` times only the device work (tt_price_run, the
 problems already resident in HBM) with CUDA events on the launching stream, L2
-flushed between steps; `e2e` times tt_price_evaluate with host buffers (host
-preparation, one host-to-device copy, kernels, one device-to-host copy).
+flushed between steps; `e2e` times tt_price_evaluate with host buffers (the
+tt_problem structs, built once from the Python objects; per step: host validation
+and derivation, one host-to-device copy, kernels, one device-to-host copy).
 The CPU baseline is the FP64 oracle (plain TT-cross in NumPy) on a bounded
 sample of the same problems, on the host cores, in spawned worker processes.
 """
@@ -560,12 +561,15 @@ def run_gpu(args):
     value = args.batch * world * args.steps / total_s
 
     # ---- end to end through the public API: tt_price_evaluate with host buffers ----
+    # (the tt_problem structs are the host buffers: built once from the Python objects;
+    # each step validates and derives on the host, copies in, runs and copies out)
+    host_batch = ttprice.ProblemBatch(problems)
     for _ in range(max(1, args.warmup // 2)):
-        pr.evaluate(problems)
+        pr.evaluate(host_batch)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        rc_e, p_e, _ = pr.evaluate(problems)
+        rc_e, p_e, _ = pr.evaluate(host_batch)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     h2d, d2h = pr.transfer_bytes()

@@ -355,7 +355,8 @@ class Pricer:
 
     # --- the C calls, one to one ---
     def prepare(self, problems) -> int:
-        self._batch = ProblemBatch(problems)
+        """Stage a batch: Problem objects, or a ProblemBatch (host structs built once)."""
+        self._batch = problems if isinstance(problems, ProblemBatch) else ProblemBatch(problems)
         return self.lib.tt_price_prepare(self.handle, self._batch.arr, self._batch.count)
 
     def run(self) -> int:
@@ -386,8 +387,9 @@ class Pricer:
         return np.frombuffer(buf, dtype=np.uint16, count=n).copy()
 
     def evaluate(self, problems):
-        """Price a batch; returns (worst status, prices ndarray, sequence of Diag)."""
-        batch = ProblemBatch(problems)
+        """Price a batch (Problem objects, or a ProblemBatch of host structs built once);
+        returns (worst status, prices ndarray, sequence of Diag)."""
+        batch = problems if isinstance(problems, ProblemBatch) else ProblemBatch(problems)
         n = batch.count
         prices = (ctypes.c_double * max(1, n))()
         diags = (tt_diag * max(1, n))()
