@@ -193,8 +193,9 @@ typedef struct {
   double imag_part;      /* Im of the discrete sum; 0 up to the TT error           */
   double flops;          /* arithmetic of the elimination, maxvol, interpolation
                             and integrand steps, by formula: 24 per integrand
-                            evaluation, 8 per complex multiply-add, 8 r^3/3 per
-                            FP64 interpolation solve                             */
+                            evaluation, 8 per complex multiply-add, 8 r^3/3 + 8 r'r
+                            per interpolation solve (w = v S, then y P = w as an
+                            elimination would count it, however it is solved)   */
   double est_discretization_err; /* estimated |grid price - integral| (absolute,
                             price units) from the Poisson-summation model of the
                             midpoint rule (Eq. discr): each axis aliases at rate
