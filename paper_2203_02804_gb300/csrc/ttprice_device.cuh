@@ -343,16 +343,19 @@ __device__ void column_shifts(Ctx<R>& x, int no, int nc) {
   if constexpr (Num<R>::kScaleColumns) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, N = x.n, m = no * N;
     for (int c = warp; c < nc; c += kWarps) {
-      // four independent maxima per lane (a max does not depend on its order)
+      // four independent maxima per lane (a max does not depend on its order), rows
+      // walked as (outer index, grid index): no integer division
       R m0 = R(-3.0e38), m1 = R(-3.0e38), m2 = R(-3.0e38), m3 = R(-3.0e38);
-      int r = lane;
-      for (; r + 96 < m; r += 128) {
-        m0 = fmax(m0, eval_logmag(x, r / N, r % N, c));
-        m1 = fmax(m1, eval_logmag(x, (r + 32) / N, (r + 32) % N, c));
-        m2 = fmax(m2, eval_logmag(x, (r + 64) / N, (r + 64) % N, c));
-        m3 = fmax(m3, eval_logmag(x, (r + 96) / N, (r + 96) % N, c));
+      for (int o = 0; o < no; ++o) {
+        int i = lane;
+        for (; i + 96 < N; i += 128) {
+          m0 = fmax(m0, eval_logmag(x, o, i, c));
+          m1 = fmax(m1, eval_logmag(x, o, i + 32, c));
+          m2 = fmax(m2, eval_logmag(x, o, i + 64, c));
+          m3 = fmax(m3, eval_logmag(x, o, i + 96, c));
+        }
+        for (; i < N; i += 32) m0 = fmax(m0, eval_logmag(x, o, i, c));
       }
-      for (; r < m; r += 32) m0 = fmax(m0, eval_logmag(x, r / N, r % N, c));
       R mx = fmax(fmax(m0, m1), fmax(m2, m3));
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
@@ -712,7 +715,29 @@ __device__ int tournament(Ctx<R>& x, int m, int nc, int b, R thr2) {
       const int t = idx % rho, c = idx / rho;
       x.sw[c * ldq + t] = x.wvals[c * x.rall + t];
     }
-    {
+    if (bs <= kThreads / 2) {
+      // two threads per candidate row, each every other column: the row's indices and
+      // grid-index table once, four independent points at a time (loads before stores)
+      const int r = tid & (kThreads / 2 - 1);
+      if (r < bs) {
+        const int g = screened ? x.scand[r] : rs + r;
+        const int o = g / N;
+        const RowTab<R> rt = row_tab(x, g - o * N);
+        cpx<R>* dst = x.sw + rho + r;
+        int c = tid / (kThreads / 2);
+        for (; c + 6 < nc; c += 8) {
+          const cpx<R> v0 = eval_row_point(x, rt, o, c);
+          const cpx<R> v1 = eval_row_point(x, rt, o, c + 2);
+          const cpx<R> v2 = eval_row_point(x, rt, o, c + 4);
+          const cpx<R> v3 = eval_row_point(x, rt, o, c + 6);
+          dst[c * ldq] = v0;
+          dst[(c + 2) * ldq] = v1;
+          dst[(c + 4) * ldq] = v2;
+          dst[(c + 6) * ldq] = v3;
+        }
+        for (; c < nc; c += 2) dst[c * ldq] = eval_row_point(x, rt, o, c);
+      }
+    } else {
       // four independent evaluations per thread and iteration (loads before stores)
       const int tot = bs * nc;
       for (int base = tid; base < tot; base += 4 * kThreads) {
@@ -929,12 +954,53 @@ __device__ void bound_prepare(float* cb, int nb, int rho, int j, const cpx<R>* B
 __device__ __forceinline__ void bound_apply(float* cb, int nb, int rho, int beta, int j, int oldb) {
   const float* cj = cb + nb * rho;
   const float* v = cj + nb;
-  for (int idx = threadIdx.x; idx < nb * rho; idx += kThreads) {
-    const int q = idx / rho, t = idx - q * rho;
-    if (q == beta) continue;
-    float nv = fmaf(cj[q], v[t], cb[idx]);
-    if (q == oldb) nv = fmaxf(nv, (t == j ? 1.0f : 0.0f) + v[t]);
-    cb[idx] = nv == nv ? nv : INFINITY;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = lane; t < rho; t += 32) {  // column per lane, blocks per warp: no integer division
+    const float vt = v[t];
+    for (int q = warp; q < nb; q += kWarps) {
+      if (q == beta) continue;
+      const int idx = q * rho + t;
+      float nv = fmaf(cj[q], vt, cb[idx]);
+      if (q == oldb) nv = fmaxf(nv, (t == j ? 1.0f : 0.0f) + vt);
+      cb[idx] = nv == nv ? nv : INFINITY;
+    }
+  }
+}
+
+// The rank-one update of a maxvol swap on a block of B (bs rows, column-major,
+// leading dimension b): B_rt -= B_rj (B_it - [t = j]) / B_ij, with the argmax of
+// |B_rt|^2 over the non-pivot rows.  With bs <= 128 two threads share a row (tid
+// & 127), each every other column, so no index needs an integer division; the
+// arithmetic per entry is the same either way.
+template <typename R>
+__device__ __forceinline__ void swap_update(cpx<R>* B, int b, int bs, int rho, int j, cpx<R> ipiv,
+                                            const cpx<R>* swrow, const cpx<R>* swcol, const unsigned char* inw,
+                                            R& bv, int& bi) {
+  const int tid = threadIdx.x;
+  if (bs <= kThreads / 2) {
+    const int r = tid & (kThreads / 2 - 1);
+    if (r < bs) {
+      const cpx<R> sc = swcol[r];
+      const bool cand = !inw[r];
+      for (int t = tid / (kThreads / 2); t < rho; t += 2) {
+        cpx<R> rv = swrow[t];
+        if (t == j) rv.re -= R(1);
+        cpx<R> bb = B[t * b + r];
+        cfms(bb, sc, cmul(rv, ipiv));
+        B[t * b + r] = bb;
+        if (cand) am_merge(bv, bi, cabs2(bb), r * rho + t);
+      }
+    }
+  } else {
+    for (int idx = tid; idx < bs * rho; idx += kThreads) {
+      const int r = idx % bs, t = idx / bs;
+      cpx<R> rv = swrow[t];
+      if (t == j) rv.re -= R(1);
+      cpx<R> bb = B[t * b + r];
+      cfms(bb, swcol[r], cmul(rv, ipiv));
+      B[t * b + r] = bb;
+      if (!inw[r]) am_merge(bv, bi, cabs2(bb), r * rho + t);
+    }
   }
 }
 
@@ -1139,20 +1205,16 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       const cpx<R> ipiv = crecip(x.swrow[j]);
       bv = R(-1);
       bi = INT_MAX;
-      for (int idx = tid; idx < bs * rho; idx += kThreads) {
-        const int r = idx % bs, t = idx / bs;
-        cpx<R> rv = x.swrow[t];
-        if (t == j) rv.re -= R(1);
-        cpx<R> bb = A[t * b + r];
-        cfms(bb, x.swcol[r], cmul(rv, ipiv));
-        A[t * b + r] = bb;
-        if (!inw[r]) am_merge(bv, bi, cabs2(bb), r * rho + t);
-      }
-      for (int idx = tid; idx < rho * rho; idx += kThreads) {
-        const int r = idx / rho, t = idx % rho;
-        cpx<R> rv = x.swrow[t];
-        if (t == j) rv.re -= R(1);
-        cfms(x.M[r * x.rall + t], x.mcol[r], cmul(rv, ipiv));
+      swap_update(A, b, bs, rho, j, ipiv, x.swrow, x.swcol, inw, bv, bi);
+      // P^{-1} update, column t per lane, rows per warp (no integer division)
+      {
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int t = lane; t < rho; t += 32) {
+          cpx<R> rv = x.swrow[t];
+          if (t == j) rv.re -= R(1);
+          const cpx<R> f = cmul(rv, ipiv);
+          for (int r = warp; r < rho; r += kWarps) cfms(x.M[r * x.rall + t], x.mcol[r], f);
+        }
       }
       if (tid == 0) x.flops += 8.0 * (bs + rho) * rho + 24.0 * rho;
       buf ^= 1;
@@ -1475,22 +1537,17 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
       const cpx<R> ipiv = crecip(x.swrow[j]);
       bv = R(-1);
       bi = INT_MAX;
-      for (int idx = tid; idx < bs * rho; idx += kThreads) {
-        const int r = idx % bs, t = idx / bs;
+      swap_update(B, b, bs, rho, j, ipiv, x.swrow, x.swcol, inw, bv, bi);
+      // P^{-1} update, column t per lane, rows per warp (no integer division)
+      for (int t = lane; t < rho; t += 32) {
         cpx<R> rv = x.swrow[t];
         if (t == j) rv.re -= R(1);
-        cpx<R> bb = B[t * b + r];
-        cfms(bb, x.swcol[r], cmul(rv, ipiv));
-        B[t * b + r] = bb;
-        if (!inw[r]) am_merge(bv, bi, cabs2(bb), r * rho + t);
-      }
-      for (int idx = tid; idx < rho * rho; idx += kThreads) {
-        const int r = idx / rho, t = idx % rho;
-        cpx<R> rv = x.swrow[t];
-        if (t == j) rv.re -= R(1);
-        cpx<R> mv = minv_get(x, kp, r, t);
-        cfms(mv, x.mcol[r], cmul(rv, ipiv));
-        minv_set(x, kp, r, t, mv);
+        const cpx<R> f = cmul(rv, ipiv);
+        for (int r = warp; r < rho; r += kWarps) {
+          cpx<R> mv = minv_get(x, kp, r, t);
+          cfms(mv, x.mcol[r], f);
+          minv_set(x, kp, r, t, mv);
+        }
       }
       if (tid == 0) x.flops += 8.0 * (bs + 2 * rho) * rho + 24.0 * rho;
       buf ^= 1;
