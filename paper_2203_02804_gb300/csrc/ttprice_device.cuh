@@ -500,11 +500,12 @@ __device__ bool invert_pivots(Ctx<R>& x, int rho) {
   const int w2 = 2 * rho, ld = w2 + 1;  // odd row stride: column accesses are conflict-free
   cpx<R>* G = x.sw;
   int* order = x.selr;
-  for (int idx = tid; idx < rho * rho; idx += kThreads) {
-    const int r = idx / rho, c = idx % rho;
-    G[r * ld + c] = x.P[r * x.rall + c];
-    G[r * ld + rho + c] = cpx<R>{R(r == c), R(0)};
-  }
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int c = lane; c < rho; c += 32)  // column per lane, rows per warp
+    for (int r = warp; r < rho; r += kWarps) {
+      G[r * ld + c] = x.P[r * x.rall + c];
+      G[r * ld + rho + c] = cpx<R>{R(r == c), R(0)};
+    }
   __syncthreads();
   const int tpr = rho <= 32 ? 8 : 4;  // threads per row (rho <= 64)
   const int myr = tid / tpr, part = tid % tpr;
@@ -542,20 +543,21 @@ __device__ bool invert_pivots(Ctx<R>& x, int rho) {
     if constexpr (TC) {
       // the tensor-core operand: hi and lo K-major planes, zero outside rho x rho
       const int kp = tc::pad16(rho);
-      for (int idx = tid; idx < kp * kp; idx += kThreads) {
-        const int r = idx / kp, c = idx % kp;
-        cpx<R> m = {R(0), R(0)};
-        if (r < rho && c < rho) {
-          const int pr = order[r];
-          m = cmul(G[pr * ld + rho + c], crecip(G[pr * ld + r]));
+      for (int c = lane; c < kp; c += 32)
+        for (int r = warp; r < kp; r += kWarps) {
+          cpx<R> m = {R(0), R(0)};
+          if (r < rho && c < rho) {
+            const int pr = order[r];
+            m = cmul(G[pr * ld + rho + c], crecip(G[pr * ld + r]));
+          }
+          minv_set(x, kp, r, c, m);
         }
-        minv_set(x, kp, r, c, m);
-      }
     } else {
-      for (int idx = tid; idx < rho * rho; idx += kThreads) {
-        const int r = idx / rho, c = idx % rho, pr = order[r];
-        x.M[r * x.rall + c] = cmul(G[pr * ld + rho + c], crecip(G[pr * ld + r]));
-      }
+      for (int c = lane; c < rho; c += 32)
+        for (int r = warp; r < rho; r += kWarps) {
+          const int pr = order[r];
+          x.M[r * x.rall + c] = cmul(G[pr * ld + rho + c], crecip(G[pr * ld + r]));
+        }
     }
   }
   if (tid == 0) x.flops += 8.0 * (double)rho * rho * (2.0 * rho);
@@ -816,9 +818,9 @@ template <typename R>
 __device__ int rank_reveal(Ctx<R>& x, int rho, R thr2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ld = rho + 1, tot = rho * rho;
   cpx<R>* __restrict__ G = x.sw;  // odd row stride: row and column reads are conflict-free
-  for (int idx = tid; idx < tot; idx += kThreads) {
-    const int j = idx / rho, t = idx % rho;
-    G[j * ld + t] = x.wvals[x.jp[t] * x.rall + j];
+  for (int t = lane; t < rho; t += 32) {  // column per lane, rows per warp
+    const int src = x.jp[t] * x.rall;
+    for (int j = warp; j < rho; j += kWarps) G[j * ld + t] = x.wvals[src + j];
   }
   __syncthreads();
   R* cm = x.colmax;  // equilibration: the column's largest |entry|^2 in the block (inf: dropped)
@@ -830,12 +832,12 @@ __device__ int rank_reveal(Ctx<R>& x, int rho, R thr2) {
     if (lane == 0) cm[t] = (mx > R(0) && mx > thr2 * x.cref[x.jp[t]]) ? mx : R(INFINITY);
   }
   __syncthreads();
+  // entry (j, t) carries index 64 j + t (rho <= 64): row-major order for ties, and
+  // decoded by shifts
   R v = R(-1);
   int vi = INT_MAX;
-  for (int idx = tid; idx < tot; idx += kThreads) {
-    const int j = idx / rho, t = idx % rho;
-    am_merge(v, vi, cabs2(G[j * ld + t]) / cm[t], idx);
-  }
+  for (int t = lane; t < rho; t += 32)
+    for (int j = warp; j < rho; j += kWarps) am_merge(v, vi, cabs2(G[j * ld + t]) / cm[t], (j << 6) | t);
   int buf = 0;
   block_argmax(v, vi, x.redv, x.redi, buf);
   unsigned long long free_r = ~0ull, free_c = ~0ull;  // rho <= 64
@@ -843,7 +845,7 @@ __device__ int rank_reveal(Ctx<R>& x, int rho, R thr2) {
   long long fl = 0;
   // v, vi and the masks are block-uniform: every thread runs the same steps
   while (k < rho && v > thr2) {
-    const int p = vi / rho, c = vi % rho;
+    const int p = vi >> 6, c = vi & 63;
     if (tid == 0) {
       x.selr[k] = p;
       x.selc[k] = c;
@@ -856,13 +858,16 @@ __device__ int rank_reveal(Ctx<R>& x, int rho, R thr2) {
     const cpx<R> ip = crecip(G[p * ld + c]);
     v = R(-1);
     vi = INT_MAX;
-    for (int idx = tid; idx < tot; idx += kThreads) {
-      const int r = idx / rho, j = idx % rho;
-      if ((free_r >> r & 1ull) && (free_c >> j & 1ull)) {
-        cpx<R> a = G[r * ld + j];
-        cfms(a, cmul(G[r * ld + c], ip), G[p * ld + j]);
-        G[r * ld + j] = a;
-        am_merge(v, vi, cabs2(a) / cm[j], idx);
+    for (int j = lane; j < rho; j += 32) {  // column per lane, rows per warp
+      if (!(free_c >> j & 1ull)) continue;
+      const cpx<R> pj = G[p * ld + j];
+      for (int r = warp; r < rho; r += kWarps) {
+        if (free_r >> r & 1ull) {
+          cpx<R> a = G[r * ld + j];
+          cfms(a, cmul(G[r * ld + c], ip), pj);
+          G[r * ld + j] = a;
+          am_merge(v, vi, cabs2(a) / cm[j], (r << 6) | j);
+        }
       }
     }
     buf ^= 1;
@@ -988,7 +993,7 @@ __device__ __forceinline__ void swap_update(cpx<R>* B, int b, int bs, int rho, i
         cpx<R> bb = B[t * b + r];
         cfms(bb, sc, cmul(rv, ipiv));
         B[t * b + r] = bb;
-        if (cand) am_merge(bv, bi, cabs2(bb), r * rho + t);
+        if (cand) am_merge(bv, bi, cabs2(bb), (r << 6) | t);
       }
     }
   } else {
@@ -999,7 +1004,7 @@ __device__ __forceinline__ void swap_update(cpx<R>* B, int b, int bs, int rho, i
       cpx<R> bb = B[t * b + r];
       cfms(bb, swcol[r], cmul(rv, ipiv));
       B[t * b + r] = bb;
-      if (!inw[r]) am_merge(bv, bi, cabs2(bb), r * rho + t);
+      if (!inw[r]) am_merge(bv, bi, cabs2(bb), (r << 6) | t);
     }
   }
 }
@@ -1171,7 +1176,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
             const int r = r0 + rt + a * rtiles, cc = col0 + c;
             if (r < bs && cc < rho) {
               A[cc * b + r] = acc[a][c];
-              if (!inw[r]) am_merge(bv, bi, cabs2(acc[a][c]), r * rho + cc);
+              if (!inw[r]) am_merge(bv, bi, cabs2(acc[a][c]), (r << 6) | cc);
             }
           }
       }
@@ -1185,7 +1190,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
     bool swapped = false;
     for (int it = 0; it < rho; ++it) {
       if (!(bv > thr)) break;
-      const int i = bi / rho, j = bi % rho;
+      const int i = bi >> 6, j = bi & 63;  // entry (r, t) carries 64 r + t (rho <= 64)
       for (int r = tid; r < bs; r += kThreads) x.swcol[r] = A[j * b + r];
       for (int t = tid; t < rho; t += kThreads) {
         x.swrow[t] = A[t * b + i];
@@ -1504,7 +1509,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
           if (row < bs && s < rho) {
             const cpx<R> v = {dr[c] - ei[c], di[c] + er[c]};  // Re A M + i Im A M
             B[s * b + row] = v;
-            if (!inw[row]) am_merge(bv, bi, cabs2(v), row * rho + s);
+            if (!inw[row]) am_merge(bv, bi, cabs2(v), (row << 6) | s);
           }
         }
       }
@@ -1517,7 +1522,7 @@ __device__ void maxvol_refine_tc(Ctx<R>& x, int m, int no, int rho, int b, R thr
     bool swapped = false;
     for (int it = 0; it < rho; ++it) {
       if (!(bv > thr)) break;
-      const int i = bi / rho, j = bi % rho;
+      const int i = bi >> 6, j = bi & 63;  // entry (r, t) carries 64 r + t (rho <= 64)
       for (int r = tid; r < bs; r += kThreads) x.swcol[r] = B[j * b + r];
       for (int t = tid; t < rho; t += kThreads) {
         x.swrow[t] = B[t * b + i];
@@ -1660,10 +1665,11 @@ __device__ bool chain_refine(Ctx<R>& x, int no, int rho) {
     y[out] = make_double2(0.0, 0.0);
     wn = s.x * s.x + s.y * s.y;
   }
-  for (int idx = tid; idx < rho * rho; idx += kThreads) {
-    const cpx<R> p = x.P[(idx / rho) * x.rall + idx % rho];
-    Pd[idx] = make_double2((double)p.re, (double)p.im);
-  }
+  for (int c = lane; c < rho; c += 32)  // column per lane, rows per warp
+    for (int r = warp; r < rho; r += kWarps) {
+      const cpx<R> p = x.P[r * x.rall + c];
+      Pd[r * rho + c] = make_double2((double)p.re, (double)p.im);
+    }
   for (int off = 16; off > 0; off >>= 1) wn = fmax(wn, __shfl_xor_sync(0xffffffffu, wn, off));
   if (lane == 0) red[2 * kWarps + warp] = wn;
   __syncthreads();
