@@ -1227,7 +1227,9 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       swapped = true;
       ++since_inv;
       ++nswaps;
+      TTP_COUNT(20, 1);
     }
+    TTP_COUNT(19, clock64() - t_sw);  // the visit's swaps (cycles)
     if (cbon && !frozen) bound_store(x.cb, beta, A, b, bs, rho, inw);
     quiet = swapped ? 0 : quiet + 1;
     ++visits;
