@@ -16,8 +16,12 @@ Every candidate prices the same seeded synthetic batch of the shape (three
 persistent waves of the full grid, through a CUDA graph), warmed up, and is
 timed with CUDA events.  Accuracy is judged against the library's own FP64
 path on the same batch: a mixed candidate counts only if every price is within
-1e-4 of it (plus 2e-7 of the largest spot, the FP32 floor of prices far below
-the spot), an FP64 candidate within 1e-6.  The fastest accepted candidate wins.
+half of 1e-4 of it (plus 2e-7 of the largest spot, the FP32 floor of prices far
+below the spot), an FP64 candidate within half of 1e-6: the batch a configuration
+then serves is not the sample, and the factor 2 covers its worst prices (at rank
+threshold 1e-5, 3 of 4096 d=5 problems outside a tuning sample within tolerance
+exceeded 1e-4).  The fastest accepted candidate wins; each record carries its
+largest error in units of the tolerance (`err_ratio`).
 
 A heterogeneous launch uses one configuration per class of problems
 (`tune_classes`): the problems are grouped by rank cap and payoff, each class
@@ -40,6 +44,9 @@ import numpy as np
 
 TOL = {"fp64": 1e-6, "mixed": 1e-4}
 FLOOR = {"fp64": 0.0, "mixed": 2e-7}       # absolute, times the largest spot
+# the sample's prices must sit within this share of the tolerance: the batch a
+# configuration then serves is not the sample, and its worst price may be worse
+MARGIN = 0.5
 RANK_TOLS = {"fp64": (1e-8,), "mixed": (1e-6, 3e-6, 1e-5)}
 KNOBS = ("block_rows", "engine", "rank_tol")
 
@@ -86,18 +93,29 @@ def candidates(precision: str, rank: int, engines: Optional[Sequence[str]] = Non
     return out
 
 
-def accepted(prices: np.ndarray, ref: np.ndarray, spot_max: np.ndarray, precision: str,
-             mask: Optional[np.ndarray] = None) -> bool:
-    """Every price finite, and every price of `mask` (the problems whose FP64 reference
-    converged; default all) within the precision's tolerance of that reference.  An
+def error_ratio(prices: np.ndarray, ref: np.ndarray, spot_max: np.ndarray, precision: str,
+                mask: Optional[np.ndarray] = None) -> float:
+    """The largest error against the reference over the problems of `mask` (those whose
+    FP64 reference converged; default all), in units of the precision's tolerance
+    (TOL relative + FLOOR x spot); infinity when a price is not finite.  An
     unconverged, rank-limited train moves by its TT error with any pivot change, so
     it says nothing about a knob."""
     if prices.size == 0:
-        return True
+        return 0.0
+    if not np.all(np.isfinite(prices)):
+        return float("inf")
     m = np.ones(prices.shape, dtype=bool) if mask is None else mask
+    if not np.any(m):
+        return 0.0
     err = np.abs(prices - ref)[m]
     bound = TOL[precision] * np.abs(ref)[m] + FLOOR[precision] * spot_max[m]
-    return bool(np.all(np.isfinite(prices)) and np.all(err <= bound))
+    return float(np.max(err / bound))
+
+
+def accepted(prices: np.ndarray, ref: np.ndarray, spot_max: np.ndarray, precision: str,
+             mask: Optional[np.ndarray] = None) -> bool:
+    """Every price finite and within MARGIN of the tolerance of the reference."""
+    return error_ratio(prices, ref, spot_max, precision, mask) <= MARGIN
 
 
 def choose(cands: Sequence[dict], measure: Callable[[dict], Tuple[float, np.ndarray]],
@@ -108,7 +126,8 @@ def choose(cands: Sequence[dict], measure: Callable[[dict], Tuple[float, np.ndar
     records = []
     for c in cands:
         secs, prices = measure(c)
-        records.append(dict(c, seconds=secs, agrees=accepted(prices, ref, spot_max, precision, mask)))
+        ratio = error_ratio(prices, ref, spot_max, precision, mask)
+        records.append(dict(c, seconds=secs, err_ratio=ratio, agrees=ratio <= MARGIN))
     valid = [r for r in records if r["agrees"]]
     if not valid:  # nothing meets the tolerance: the most accurate threshold, fastest of those
         tightest = min(r["rank_tol"] for r in records)

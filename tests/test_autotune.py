@@ -33,6 +33,9 @@ def test_choose_takes_the_fastest_the_fp64_reference_accepts():
     # the FP32 floor: a tiny price may be off by 2e-7 of the spot
     assert autotune.accepted(np.array([1e-3 + 1e-5]), np.array([1e-3]), np.array([100.0]), "mixed")
     assert not autotune.accepted(np.array([1e-3 + 1e-4]), np.array([1e-3]), np.array([100.0]), "mixed")
+    # within the tolerance but past its margin (the served batch is not the sample): refused
+    assert not autotune.accepted(ref * (1 + 8e-5), ref, spot, "mixed")
+    assert autotune.error_ratio(ref * (1 + 8e-5), ref, spot, "mixed") < 1.0
     # nothing accepted: the tightest threshold, fastest of those
     best, _ = autotune.choose(cands, lambda c: (1.0 if c["block_rows"] == 64 else 2.0, ref * 1.1), ref, spot, "mixed")
     assert best["rank_tol"] == 1e-6 and best["block_rows"] == 64
