@@ -1618,7 +1618,7 @@ __device__ __forceinline__ cpx<R> minv_at(const Ctx<R>& x, int kp, int t, int s)
   }
 }
 
-constexpr int kRefineIters = 8;
+constexpr int kRefineIters = 12;
 
 // y P = w (w = v S, the contraction's row vector) by iterative refinement on
 // maxvol's running inverse M ~ P^{-1}: y_0 = 0, r_0 = w; then d = r M in R,
