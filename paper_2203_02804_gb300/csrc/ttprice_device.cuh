@@ -931,8 +931,13 @@ __device__ void bound_store(float* cb, int beta, const cpx<R>* B, int b, int bs,
     R mx = R(0);
     for (int r = lane; r < bs; r += 32)
       if (!inw[r]) mx = fmax(mx, cabs2(B[t * b + r]));
+    if constexpr (sizeof(R) == 4) {
+      // non-negative floats order like their bits (a NaN above all: no skip then)
+      mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+    } else {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
     if (lane == 0) cb[beta * rho + t] = (mx == mx) ? sqrtf((float)mx) * 1.0001f : INFINITY;
   }
 }
@@ -1139,6 +1144,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
       }
     }
     // B = A M in row strips; each strip is read completely before it is overwritten
+    TTP_TIC(t_prod);
     R bv = R(-1);
     int bi = INT_MAX;
     for (int r0 = 0; r0 < (frozen ? 0 : bs); r0 += rpr) {
@@ -1181,6 +1187,7 @@ __device__ void maxvol_refine(Ctx<R>& x, int m, int no, int rho, int b, R thr) {
           }
       }
     }
+    TTP_COUNT(21, clock64() - t_prod);  // the block product and its stores (cycles)
     if (!frozen) {  // block-uniform
       buf ^= 1;
       block_argmax(bv, bi, x.redv, x.redi, buf);

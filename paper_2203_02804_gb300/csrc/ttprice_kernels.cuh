@@ -54,8 +54,10 @@ constexpr int kWarps = kThreads / 32;
 
 enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NUMERIC = -6, ST_INVALID = -1 };
 
+// aligned as a pair, so that one complex moves in one 8-byte (FP32) or 16-byte
+// (FP64) load or store; every cpx array starts on such a boundary
 template <typename R>
-struct cpx {
+struct alignas(2 * sizeof(R)) cpx {
   R re, im;
 };
 

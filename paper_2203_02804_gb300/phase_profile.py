@@ -69,7 +69,8 @@ def main():
             print(f"{name:44s} {buf[i] / args.batch / 1e6:8.3f} Mcycles/price {100 * buf[i] / tot:6.2f}%")
     if buf[20]:
         print(f"maxvol (CUDA-core engine): {buf[20]} swaps, {buf[19] / buf[20] / 1e3:.1f} kcycles of swap loop "
-              f"per swap, {(buf[9] - buf[19]) / 1e3 / args.batch:.1f} kcycles per price of visit tails")
+              f"per swap, {(buf[9] - buf[19]) / 1e3 / args.batch:.1f} kcycles per price of visit tails; "
+              f"block product loop {buf[21] / args.batch / 1e6:.3f} Mcycles per price")
     if buf[16]:
         print(f"interpolation solves: {buf[16]}, by refinement {buf[16] - buf[17]} "
               f"({buf[18] / buf[16]:.2f} steps each), by elimination {buf[17]}")
