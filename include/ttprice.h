@@ -50,7 +50,9 @@ typedef enum { TT_MIN_CALL = 0, TT_MAX_CALL = 1 } tt_payoff;
 
 /* TT_FP64: every step in FP64.
  * TT_MIXED: integrand values, elimination and maxvol in FP32 complex; the phase
- * and exponent arguments, the interpolation solve and the contraction in FP64. */
+ * and exponent arguments, the contraction and the interpolation solve in FP64
+ * (refined from maxvol's FP32 inverse with FP64 residuals to the FP64 solution,
+ * FP64 elimination when the refinement does not converge). */
 typedef enum { TT_FP64 = 0, TT_MIXED = 1 } tt_precision;
 
 /* Engine of the maxvol block product in the mixed path (Section IV.B cross step):
