@@ -1625,7 +1625,10 @@ __device__ __forceinline__ cpx<R> minv_at(const Ctx<R>& x, int kp, int t, int s)
   }
 }
 
-constexpr int kRefineIters = 12;
+#ifndef TTP_REFINE_ITERS
+#define TTP_REFINE_ITERS 12
+#endif
+constexpr int kRefineIters = TTP_REFINE_ITERS;  // a build with 0 solves every system by elimination
 
 // y P = w (w = v S, the contraction's row vector) by iterative refinement on
 // maxvol's running inverse M ~ P^{-1}: y_0 = 0, r_0 = w; then d = r M in R,
