@@ -110,3 +110,19 @@ def test_gpu_class_tuning_drives_one_heterogeneous_launch():
     # rank-limited trains part from the FP64 path by their TT error; most are converged
     rel = np.abs(got / ref - 1)
     assert np.median(rel) < 1e-4 and np.all(rel < 5e-2)
+
+
+def test_error_ratio_edge_cases():
+    ref = np.array([1.0, 2.0])
+    spot = np.array([100.0, 100.0])
+    # a non-finite price refuses the candidate whatever the others do
+    assert autotune.error_ratio(np.array([1.0, np.nan]), ref, spot, "mixed") == float("inf")
+    assert not autotune.accepted(np.array([1.0, np.inf]), ref, spot, "mixed")
+    # only the problems of the mask count (unconverged FP64 references say nothing)
+    off = np.array([1.0 + 1e-2, 2.0])
+    assert autotune.error_ratio(off, ref, spot, "mixed", mask=np.array([False, True])) == 0.0
+    assert autotune.error_ratio(off, ref, spot, "mixed", mask=np.array([False, False])) == 0.0
+    # in units of the tolerance: 1e-4 relative + 2e-7 x spot
+    r = autotune.error_ratio(np.array([1.0 + 6e-5]), np.array([1.0]), np.array([100.0]), "mixed")
+    assert abs(r - 6e-5 / (1e-4 + 2e-5)) < 1e-9
+    assert autotune.error_ratio(np.array([]), np.array([]), np.array([]), "mixed") == 0.0
